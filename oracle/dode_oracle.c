@@ -1,0 +1,558 @@
+/*
+ * dode_oracle.c -- plain, slow, FP64 reference of the per-day DODE / SPGD path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product links, loads or calls this
+ * file: only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark do.  It shares no code, header or table with the CUDA library.
+ *
+ * Every function follows one passage of Ma & Qian, "Estimating multi-year 24/7
+ * origin-destination demand using high-granular multi-source traffic data"
+ * (arXiv 1901.09266).  Equations are named by their labels in the paper's
+ * source: Eq. (cost) is the path travel time by link composition (Sec. 2.4),
+ * Eq. (dar) the DAR ratio (Sec. 2.3), Eq. (logit) / (rt) / (flow) the route
+ * choice (Sec. 2.6), Eq. (assign) the assignment matrix and Eq. (opt) / (nnls)
+ * the NNLS problem (Sec. 2.7 and 3), Algorithm 1 the SPGD method (Sec. 3.3).
+ *
+ * Readings of points the paper leaves open (all listed in the design notes):
+ *  - time is counted in integer ticks; tps ticks per second, ipt ticks per
+ *    interval (16 and 4800 for 5-minute intervals);
+ *  - link travel time is taken at the link entry interval (Sec. 2.4, the
+ *    omega_1 = t^2 - (t^1 + c_1(t^1)) relation) and quantised once, in FP32,
+ *    to ticks: c = rint(fl32(fl32(len * 3600 tps) / v)), at least 1 tick;
+ *  - a link is observed at its tail (entry), intervals are half open
+ *    [t^h, t^{h+1}), mass arriving at or after the end of the day is dropped
+ *    (Sec. 2.7, per-day decomposition);
+ *  - FIFO (Sec. 2.2) is enforced by a running maximum over departures;
+ *  - the route time of departure interval h1 is the leading vehicle's
+ *    (departing at t^{h1}) time to the end of the route, in minutes;
+ *  - Adagrad (Duchi et al.) with G_0 = 0, q_0 = 0 (unless given), no decay;
+ *    g = B^T (B q - x) without the factor 2, exactly as Algorithm 1 prints it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ERR_ARG -1
+#define OR_ERR_BAD_SPEED -4
+#define OR_ERR_TICK_OVERFLOW -5
+#define OR_ERR_OOM -6
+
+/* ------------------------------------------------------------------------ */
+/* Network + routes (caller-owned arrays, copied)                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t N;          /* intervals per day */
+    int32_t ipt;        /* ticks per interval */
+    int32_t tps;        /* ticks per second */
+    int32_t A;          /* links */
+    float *len_mi;      /* [A] */
+    int32_t P;          /* routes */
+    int32_t K;          /* OD pairs */
+    int32_t *rptr;      /* [P+1] */
+    int32_t *rlinks;    /* [rptr[P]] */
+    int32_t *rod;       /* [P] */
+    int32_t O;          /* observed links */
+    int32_t *obs_col;   /* [A]: column of link a in the observation order, -1 if unobserved */
+} or_net;
+
+/* One DAR entry rho_{rs}^{ka}(h1, h2) of route k at its j-th link (Eq. (dar)). */
+typedef struct {
+    int32_t k, j, h1, h2;
+    double rho;
+} or_dar_entry;
+
+/* One day's model: everything the speeds determine. */
+typedef struct {
+    const or_net *net;
+    int32_t *ticks;       /* [N][A] link travel time in ticks, by entry interval */
+    int64_t *T;           /* [(rptr[k]+k+j)][N+1] trajectory times, j = 0..beta_k */
+    int64_t n_repairs;    /* FIFO repairs applied */
+    or_dar_entry *dar;    /* DAR entries */
+    int64_t n_dar;
+    double *C;            /* [N][P] route time of departure interval h1, minutes */
+    double theta;
+    double *p;            /* [N][P] route choice portion */
+    /* assignment matrix B (Eq. (assign)) in COO, observed rows only */
+    int64_t nnz;
+    int32_t *b_row;       /* h2 * O + o */
+    int32_t *b_col;       /* h1 * K + od */
+    double *b_val;
+} or_day;
+
+or_net *or_net_create(int32_t N, int32_t interval_s, int32_t tps, int32_t A, const float *len_mi,
+                      int32_t P, int32_t K, const int32_t *rptr, const int32_t *rlinks,
+                      const int32_t *rod, int32_t O, const int32_t *obs_links) {
+    if (N <= 0 || interval_s <= 0 || tps <= 0 || A <= 0 || P <= 0 || K <= 0 || O < 0) return NULL;
+    or_net *n = (or_net *)calloc(1, sizeof(or_net));
+    n->N = N;
+    n->ipt = interval_s * tps;
+    n->tps = tps;
+    n->A = A;
+    n->P = P;
+    n->K = K;
+    n->O = O;
+    n->len_mi = (float *)malloc(sizeof(float) * A);
+    memcpy(n->len_mi, len_mi, sizeof(float) * A);
+    n->rptr = (int32_t *)malloc(sizeof(int32_t) * (P + 1));
+    memcpy(n->rptr, rptr, sizeof(int32_t) * (P + 1));
+    n->rlinks = (int32_t *)malloc(sizeof(int32_t) * (rptr[P] > 0 ? rptr[P] : 1));
+    memcpy(n->rlinks, rlinks, sizeof(int32_t) * rptr[P]);
+    n->rod = (int32_t *)malloc(sizeof(int32_t) * P);
+    memcpy(n->rod, rod, sizeof(int32_t) * P);
+    n->obs_col = (int32_t *)malloc(sizeof(int32_t) * A);
+    for (int32_t a = 0; a < A; ++a) n->obs_col[a] = -1;
+    for (int32_t o = 0; o < O; ++o) n->obs_col[obs_links[o]] = o;
+    return n;
+}
+
+void or_net_destroy(or_net *n) {
+    if (!n) return;
+    free(n->len_mi); free(n->rptr); free(n->rlinks); free(n->rod); free(n->obs_col);
+    free(n);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 1 -- link travel times from probe speeds (Sec. 2.4, last paragraph): */
+/* the travel time of link a entered in interval h, in integer ticks.       */
+/* The quantisation is done in IEEE FP32 (multiply, divide, round to        */
+/* nearest even) so that any implementation reproduces the same integers.  */
+/* ------------------------------------------------------------------------ */
+int or_ticks(const or_net *n, const float *speed_mph /* [N][A] */, int32_t *ticks /* [N][A] */) {
+    const float scale = (float)(n->tps * 3600);
+    for (int32_t h = 0; h < n->N; ++h) {
+        for (int32_t a = 0; a < n->A; ++a) {
+            float v = speed_mph[(size_t)h * n->A + a];
+            if (!(v > 0.0f) || !isfinite(v)) return OR_ERR_BAD_SPEED;
+            volatile float num = n->len_mi[a] * scale;  /* fl32(len * 3600 tps) */
+            volatile float t = num / v;                  /* fl32(num / v) */
+            if (!(t <= 16777216.0f)) return OR_ERR_TICK_OVERFLOW;
+            float r = nearbyintf(t);                      /* round half to even */
+            int32_t c = (int32_t)r;
+            ticks[(size_t)h * n->A + a] = c < 1 ? 1 : c;
+        }
+    }
+    return OR_OK;
+}
+
+/* c_a(t): travel time of link a for a vehicle entering it at tick t.       */
+static int64_t link_time(const or_net *n, const int32_t *ticks, int32_t a, int64_t t) {
+    int64_t h = t / n->ipt;
+    if (h > n->N - 1) h = n->N - 1;
+    return ticks[h * n->A + a];
+}
+
+static size_t traj_index(const or_net *n, int32_t k, int32_t j, int32_t b) {
+    return ((size_t)(n->rptr[k] + k + j)) * (size_t)(n->N + 1) + (size_t)b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 2 -- leading-vehicle trajectories (Example "DAR matrix computation", */
+/* Eq. (cost)).  T_{k,0}(b) = t^b is the departure at interval boundary b;   */
+/* T_{k,j+1}(b) = T_{k,j}(b) + c_{a_{k,j}}(T_{k,j}(b)).  FIFO (Sec. 2.2) is   */
+/* enforced per link, in increasing b, by T_{k,j}(b) >= T_{k,j}(b-1).        */
+/* ------------------------------------------------------------------------ */
+void or_trajectories(const or_net *n, const int32_t *ticks, int64_t *T, int64_t *n_repairs) {
+    int64_t rep = 0;
+    for (int32_t k = 0; k < n->P; ++k) {
+        int32_t beta = n->rptr[k + 1] - n->rptr[k];
+        for (int32_t b = 0; b <= n->N; ++b) {
+            T[traj_index(n, k, 0, b)] = (int64_t)n->ipt * b;
+            for (int32_t j = 0; j < beta; ++j) {
+                int32_t a = n->rlinks[n->rptr[k] + j];
+                int64_t t = T[traj_index(n, k, j, b)];
+                int64_t nxt = t + link_time(n, ticks, a, t);
+                if (b > 0) {
+                    int64_t prev = T[traj_index(n, k, j + 1, b - 1)];
+                    if (nxt < prev) { nxt = prev; ++rep; }
+                }
+                T[traj_index(n, k, j + 1, b)] = nxt;
+            }
+        }
+    }
+    *n_repairs = rep;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 3 -- DAR (Eq. (dar)): flow of route k departing in H_{h1} reaches    */
+/* the tail of its j-th link spread evenly (Eq. (unif)) over the window     */
+/* [T_{k,j}(h1), T_{k,j}(h1+1)); rho(h1,h2) is the share of that window in   */
+/* H_{h2}.  A zero-length window puts all mass in the interval containing   */
+/* it.  Shares at h2 >= N (after midnight) are dropped.                     */
+/* ------------------------------------------------------------------------ */
+static int64_t dar_emit(const or_net *n, const int64_t *T, or_dar_entry *out) {
+    int64_t m = 0;
+    const int64_t ipt = n->ipt;
+    for (int32_t k = 0; k < n->P; ++k) {
+        int32_t beta = n->rptr[k + 1] - n->rptr[k];
+        for (int32_t j = 0; j < beta; ++j) {
+            for (int32_t h1 = 0; h1 < n->N; ++h1) {
+                int64_t lo = T[traj_index(n, k, j, h1)];
+                int64_t hi = T[traj_index(n, k, j, h1 + 1)];
+                if (hi == lo) {
+                    int64_t h2 = lo / ipt;
+                    if (h2 < n->N) {
+                        if (out) { out[m].k = k; out[m].j = j; out[m].h1 = h1; out[m].h2 = (int32_t)h2; out[m].rho = 1.0; }
+                        ++m;
+                    }
+                    continue;
+                }
+                for (int64_t h2 = lo / ipt; h2 <= (hi - 1) / ipt && h2 < n->N; ++h2) {
+                    int64_t s = lo > ipt * h2 ? lo : ipt * h2;
+                    int64_t e = hi < ipt * (h2 + 1) ? hi : ipt * (h2 + 1);
+                    if (out) {
+                        out[m].k = k; out[m].j = j; out[m].h1 = h1; out[m].h2 = (int32_t)h2;
+                        out[m].rho = (double)(e - s) / (double)(hi - lo);
+                    }
+                    ++m;
+                }
+            }
+        }
+    }
+    return m;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 4 -- route choice (Eq. (logit), (rt)): logit over the routes of one  */
+/* OD pair on the route time of the leading vehicle of interval h1.         */
+/* ------------------------------------------------------------------------ */
+static void route_choice(const or_net *n, const double *C, double theta, double *p) {
+    for (int32_t h = 0; h < n->N; ++h) {
+        for (int32_t od = 0; od < n->K; ++od) {
+            double mx = -INFINITY, den = 0.0;
+            for (int32_t k = 0; k < n->P; ++k)
+                if (n->rod[k] == od && -theta * C[(size_t)h * n->P + k] > mx) mx = -theta * C[(size_t)h * n->P + k];
+            for (int32_t k = 0; k < n->P; ++k)
+                if (n->rod[k] == od) den += exp(-theta * C[(size_t)h * n->P + k] - mx);
+            for (int32_t k = 0; k < n->P; ++k)
+                if (n->rod[k] == od) p[(size_t)h * n->P + k] = exp(-theta * C[(size_t)h * n->P + k] - mx) / den;
+        }
+    }
+}
+
+/* Assignment matrix entries B[(h2,o),(h1,od)] += delta rho p (Eq. (assign)). */
+static void assemble_B(or_day *d) {
+    const or_net *n = d->net;
+    int64_t nnz = 0;
+    for (int64_t e = 0; e < d->n_dar; ++e) {
+        const or_dar_entry *x = &d->dar[e];
+        int32_t a = n->rlinks[n->rptr[x->k] + x->j];
+        if (n->obs_col[a] >= 0) ++nnz;
+    }
+    free(d->b_row); free(d->b_col); free(d->b_val);
+    d->b_row = (int32_t *)malloc(sizeof(int32_t) * (nnz ? nnz : 1));
+    d->b_col = (int32_t *)malloc(sizeof(int32_t) * (nnz ? nnz : 1));
+    d->b_val = (double *)malloc(sizeof(double) * (nnz ? nnz : 1));
+    int64_t m = 0;
+    for (int64_t e = 0; e < d->n_dar; ++e) {
+        const or_dar_entry *x = &d->dar[e];
+        int32_t a = n->rlinks[n->rptr[x->k] + x->j];
+        int32_t o = n->obs_col[a];
+        if (o < 0) continue;
+        d->b_row[m] = x->h2 * n->O + o;
+        d->b_col[m] = x->h1 * n->K + n->rod[x->k];
+        d->b_val[m] = x->rho * d->p[(size_t)x->h1 * n->P + x->k];
+        ++m;
+    }
+    d->nnz = nnz;
+}
+
+/* Route-choice portions for a dispersion theta (per minute); rebuilds B.   */
+void or_day_set_theta(or_day *d, double theta) {
+    d->theta = theta;
+    route_choice(d->net, d->C, theta, d->p);
+    assemble_B(d);
+}
+
+/* Build one day's model from its speeds [N][A].  Returns NULL on error.     */
+or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int *err) {
+    or_day *d = (or_day *)calloc(1, sizeof(or_day));
+    d->net = n;
+    d->ticks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n->N * n->A);
+    int rc = or_ticks(n, speed_mph, d->ticks);
+    if (rc != OR_OK) {
+        if (err) *err = rc;
+        free(d->ticks); free(d);
+        return NULL;
+    }
+    size_t ntraj = (size_t)(n->rptr[n->P] + n->P) * (size_t)(n->N + 1);
+    d->T = (int64_t *)malloc(sizeof(int64_t) * ntraj);
+    or_trajectories(n, d->ticks, d->T, &d->n_repairs);
+    d->n_dar = dar_emit(n, d->T, NULL);
+    d->dar = (or_dar_entry *)malloc(sizeof(or_dar_entry) * (d->n_dar ? d->n_dar : 1));
+    dar_emit(n, d->T, d->dar);
+    /* route time in minutes (Eq. (cost)): end of route minus departure */
+    d->C = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
+    d->p = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
+    for (int32_t k = 0; k < n->P; ++k) {
+        int32_t beta = n->rptr[k + 1] - n->rptr[k];
+        for (int32_t h = 0; h < n->N; ++h)
+            d->C[(size_t)h * n->P + k] =
+                (double)(d->T[traj_index(n, k, beta, h)] - (int64_t)n->ipt * h) / (double)(60 * n->tps);
+    }
+    or_day_set_theta(d, theta);
+    if (err) *err = OR_OK;
+    return d;
+}
+
+void or_day_destroy(or_day *d) {
+    if (!d) return;
+    free(d->ticks); free(d->T); free(d->dar); free(d->C); free(d->p);
+    free(d->b_row); free(d->b_col); free(d->b_val);
+    free(d);
+}
+
+/* ---- accessors for tests ------------------------------------------------ */
+int64_t or_day_n_dar(const or_day *d) { return d->n_dar; }
+int64_t or_day_nnz(const or_day *d) { return d->nnz; }
+int64_t or_day_repairs(const or_day *d) { return d->n_repairs; }
+void or_day_get_ticks(const or_day *d, int32_t *out) {
+    memcpy(out, d->ticks, sizeof(int32_t) * (size_t)d->net->N * d->net->A);
+}
+void or_day_get_traj(const or_day *d, int64_t *out) {
+    const or_net *n = d->net;
+    memcpy(out, d->T, sizeof(int64_t) * (size_t)(n->rptr[n->P] + n->P) * (size_t)(n->N + 1));
+}
+void or_day_get_dar(const or_day *d, int32_t *kjh /* [n][4] */, double *rho) {
+    for (int64_t e = 0; e < d->n_dar; ++e) {
+        kjh[4 * e + 0] = d->dar[e].k; kjh[4 * e + 1] = d->dar[e].j;
+        kjh[4 * e + 2] = d->dar[e].h1; kjh[4 * e + 3] = d->dar[e].h2;
+        rho[e] = d->dar[e].rho;
+    }
+}
+void or_day_get_route_choice(const or_day *d, double *C, double *p) {
+    size_t m = (size_t)d->net->N * d->net->P;
+    if (C) memcpy(C, d->C, sizeof(double) * m);
+    if (p) memcpy(p, d->p, sizeof(double) * m);
+}
+void or_day_get_B(const or_day *d, int32_t *row, int32_t *col, double *val) {
+    memcpy(row, d->b_row, sizeof(int32_t) * d->nnz);
+    memcpy(col, d->b_col, sizeof(int32_t) * d->nnz);
+    memcpy(val, d->b_val, sizeof(double) * d->nnz);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Step 5 -- link flows implied by OD flows (Eq. (reverse) with (flow)):     */
+/* xhat = B q, rows (h2, o) in the time-major order of Table "DODE framework */
+/* variable vectorization".                                                 */
+/* ------------------------------------------------------------------------ */
+void or_forward(const or_day *d, const double *q /* [N][K] */, double *xhat /* [N][O] */) {
+    const or_net *n = d->net;
+    memset(xhat, 0, sizeof(double) * (size_t)n->N * n->O);
+    for (int64_t e = 0; e < d->nnz; ++e) xhat[d->b_row[e]] += d->b_val[e] * q[d->b_col[e]];
+}
+
+/* Step 6 -- masked residual r = m (B q - x) and loss sum r^2 (Eq. (nnls)). */
+double or_residual(const or_day *d, const double *xhat, const float *counts, const uint8_t *mask,
+                   double *r) {
+    const or_net *n = d->net;
+    double loss = 0.0;
+    for (size_t i = 0; i < (size_t)n->N * n->O; ++i) {
+        r[i] = mask[i] ? xhat[i] - (double)counts[i] : 0.0;
+        loss += r[i] * r[i];
+    }
+    return loss;
+}
+
+/* Step 7 -- g = B^T r (Algorithm 1, gradient line, without the factor 2).   */
+void or_adjoint(const or_day *d, const double *r /* [N][O] */, double *g /* [N][K] */) {
+    const or_net *n = d->net;
+    memset(g, 0, sizeof(double) * (size_t)n->N * n->K);
+    for (int64_t e = 0; e < d->nnz; ++e) g[d->b_col[e]] += d->b_val[e] * r[d->b_row[e]];
+}
+
+/* Step 8 -- Adagrad step and projection onto q >= 0 (Algorithm 1).          */
+static void adagrad_project(size_t m, const double *g, double eta, double eps, double *q, double *G) {
+    for (size_t i = 0; i < m; ++i) {
+        G[i] += g[i] * g[i];
+        q[i] -= eta * g[i] / (sqrt(G[i]) + eps);
+        if (q[i] < 0.0) q[i] = 0.0;
+    }
+}
+
+/* SplitMix64 (Steele, Lea, Flood 2014) -- the generator for the row order. */
+uint64_t or_splitmix64_next(uint64_t *state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* permutate(range(n)) of Algorithm 1 over the observed rows of one day and  */
+/* epoch: Fisher-Yates with u = top 53 bits of SplitMix64 / 2^53,           */
+/* state seeded with seed XOR (day << 32 | epoch).                          */
+void or_permute_rows(int32_t *rows, int32_t n_rows, uint64_t seed, int32_t day, int32_t epoch) {
+    uint64_t st = seed ^ (((uint64_t)(uint32_t)day << 32) | (uint64_t)(uint32_t)epoch);
+    for (int32_t i = n_rows - 1; i >= 1; --i) {
+        double u = (double)(or_splitmix64_next(&st) >> 11) * (1.0 / 9007199254740992.0);
+        int32_t j = (int32_t)(u * (double)(i + 1));
+        int32_t t = rows[i]; rows[i] = rows[j]; rows[j] = t;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 on one day.  row_chunk == 0: one full-row update per epoch;   */
+/* row_chunk = b > 0: each epoch permutes the observed rows and updates on  */
+/* consecutive chunks of b rows (last chunk partial).  q, G are in/out.     */
+/* loss_trace[e] = masked loss at the start of epoch e (may be NULL).        */
+/* Returns the masked loss of the final q.                                  */
+/* ------------------------------------------------------------------------ */
+double or_solve_day(const or_day *d, const float *counts, const uint8_t *mask, int32_t iters,
+                    double eta, double eps, int32_t row_chunk, uint64_t seed, int32_t day,
+                    double *q, double *G, double *loss_trace) {
+    const or_net *n = d->net;
+    size_t rows = (size_t)n->N * n->O, cols = (size_t)n->N * n->K;
+    double *xhat = (double *)malloc(sizeof(double) * rows);
+    double *r = (double *)malloc(sizeof(double) * rows);
+    double *g = (double *)malloc(sizeof(double) * cols);
+    int32_t *order = NULL, n_obs_rows = 0;
+    uint8_t *sel = NULL;
+    if (row_chunk > 0) {
+        order = (int32_t *)malloc(sizeof(int32_t) * (rows ? rows : 1));
+        sel = (uint8_t *)malloc(rows ? rows : 1);
+    }
+    for (int32_t e = 0; e < iters; ++e) {
+        if (row_chunk <= 0) {
+            or_forward(d, q, xhat);
+            double loss = or_residual(d, xhat, counts, mask, r);
+            if (loss_trace) loss_trace[e] = loss;
+            or_adjoint(d, r, g);
+            adagrad_project(cols, g, eta, eps, q, G);
+            continue;
+        }
+        if (loss_trace) {
+            or_forward(d, q, xhat);
+            loss_trace[e] = or_residual(d, xhat, counts, mask, r);
+        }
+        /* observed rows in ascending order, then permuted for this epoch */
+        n_obs_rows = 0;
+        for (size_t i = 0; i < rows; ++i)
+            if (mask[i]) order[n_obs_rows++] = (int32_t)i;
+        or_permute_rows(order, n_obs_rows, seed, day, e);
+        for (int32_t s = 0; s < n_obs_rows; s += row_chunk) {
+            int32_t t = s + row_chunk < n_obs_rows ? s + row_chunk : n_obs_rows;
+            memset(sel, 0, rows);
+            for (int32_t i = s; i < t; ++i) sel[order[i]] = 1;
+            or_forward(d, q, xhat);
+            or_residual(d, xhat, counts, sel, r);
+            or_adjoint(d, r, g);
+            adagrad_project(cols, g, eta, eps, q, G);
+        }
+    }
+    or_forward(d, q, xhat);
+    double loss = or_residual(d, xhat, counts, mask, r);
+    free(xhat); free(r); free(g); free(order); free(sel);
+    return loss;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Differentiable form: L(q, theta) = sum m (B q - x)^2.                     */
+/* dL/dq = 2 B^T r;  dL/dtheta through p = logit(-theta C) (Eq. (logit)):    */
+/* dp_k/dtheta = p_k (-C_k + sum_{k' in od} p_k' C_k').                      */
+/* ------------------------------------------------------------------------ */
+double or_loss_grad_day(const or_day *d, const float *counts, const uint8_t *mask, const double *q,
+                        double *dq, double *dtheta) {
+    const or_net *n = d->net;
+    size_t rows = (size_t)n->N * n->O, cols = (size_t)n->N * n->K;
+    double *xhat = (double *)malloc(sizeof(double) * rows);
+    double *r = (double *)malloc(sizeof(double) * rows);
+    or_forward(d, q, xhat);
+    double loss = or_residual(d, xhat, counts, mask, r);
+    if (dq) {
+        or_adjoint(d, r, dq);
+        for (size_t i = 0; i < cols; ++i) dq[i] *= 2.0;
+    }
+    if (dtheta) {
+        /* route-level adjoint gp[h1][k] = sum_{j,h2} rho r[h2][a_kj], observed links */
+        double *gp = (double *)calloc((size_t)n->N * n->P, sizeof(double));
+        for (int64_t e = 0; e < d->n_dar; ++e) {
+            const or_dar_entry *x = &d->dar[e];
+            int32_t o = n->obs_col[n->rlinks[n->rptr[x->k] + x->j]];
+            if (o < 0) continue;
+            gp[(size_t)x->h1 * n->P + x->k] += x->rho * r[(size_t)x->h2 * n->O + o];
+        }
+        double acc = 0.0;
+        for (int32_t h = 0; h < n->N; ++h) {
+            for (int32_t k = 0; k < n->P; ++k) {
+                int32_t od = n->rod[k];
+                double mean_c = 0.0;
+                for (int32_t k2 = 0; k2 < n->P; ++k2)
+                    if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->C[(size_t)h * n->P + k2];
+                double pk = d->p[(size_t)h * n->P + k];
+                double dp = pk * (-d->C[(size_t)h * n->P + k] + mean_c);
+                acc += 2.0 * q[(size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * dp;
+            }
+        }
+        *dtheta = acc;
+        free(gp);
+    }
+    free(xhat); free(r);
+    return loss;
+}
+
+/* Dense B (rows N*O, cols N*K) for tiny instances.                          */
+void or_day_dense_B(const or_day *d, double *Bd) {
+    const or_net *n = d->net;
+    size_t cols = (size_t)n->N * n->K;
+    memset(Bd, 0, sizeof(double) * (size_t)n->N * n->O * cols);
+    for (int64_t e = 0; e < d->nnz; ++e) Bd[(size_t)d->b_row[e] * cols + d->b_col[e]] += d->b_val[e];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-day driver: days are independent problems (Sec. 2.7), solved one   */
+/* by one (optionally several at once with OpenMP).  Inputs are [D][...]    */
+/* slabs; q_inout / G_inout are FP64 [D][N][K]; loss_out [D].                */
+/* Returns 0, or the first error code met.                                   */
+/* ------------------------------------------------------------------------ */
+int or_solve_days(const or_net *n, int32_t D, const int32_t *day_ids, const float *speeds,
+                  const float *counts, const uint8_t *mask, double theta, int32_t iters, double eta,
+                  double eps, int32_t row_chunk, uint64_t seed, int32_t n_threads, double *q_inout,
+                  double *G_inout, double *loss_out) {
+    int status = OR_OK;
+    size_t sA = (size_t)n->N * n->A, sO = (size_t)n->N * n->O, sK = (size_t)n->N * n->K;
+    (void)n_threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+#endif
+    for (int32_t i = 0; i < D; ++i) {
+        int err = OR_OK;
+        or_day *d = or_day_build(n, speeds + sA * i, theta, &err);
+        if (!d) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            { if (status == OR_OK) status = err; }
+            continue;
+        }
+        loss_out[i] = or_solve_day(d, counts + sO * i, mask + sO * i, iters, eta, eps, row_chunk, seed,
+                                   day_ids ? day_ids[i] : i, q_inout + sK * i, G_inout + sK * i, NULL);
+        or_day_destroy(d);
+    }
+    return status;
+}
+
+/* Forward for many days: xhat [D][N][O] = B_d q_d.                          */
+int or_forward_days(const or_net *n, int32_t D, const float *speeds, const double *q, double theta,
+                    int32_t n_threads, double *xhat) {
+    int status = OR_OK;
+    size_t sA = (size_t)n->N * n->A, sO = (size_t)n->N * n->O, sK = (size_t)n->N * n->K;
+    (void)n_threads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+#endif
+    for (int32_t i = 0; i < D; ++i) {
+        int err = OR_OK;
+        or_day *d = or_day_build(n, speeds + sA * i, theta, &err);
+        if (!d) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            { if (status == OR_OK) status = err; }
+            continue;
+        }
+        or_forward(d, q + sK * i, xhat + sO * i);
+        or_day_destroy(d);
+    }
+    return status;
+}

@@ -1,0 +1,422 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than its own formula: the
+paper's worked examples (tests/golden), closed forms of constant-speed
+networks, conservation, partition invariants, brute-force NNLS, exact
+recovery, finite differences and published PRNG vectors.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from oracle.nnls_ref import kkt_violation, nnls_bruteforce
+from paper_1901_09266_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _single_path_net(lengths, n_intervals, interval_s=300, tps=16, obs=None):
+    L = len(lengths)
+    obs = list(range(L)) if obs is None else obs
+    return orc.Net(n_intervals, interval_s, tps, np.asarray(lengths, np.float32), [0, L], list(range(L)),
+                   [0], 1, obs)
+
+
+# ---------------------------------------------------------------------------
+# ticks (Sec. 2.4: travel times from probe speeds)
+# ---------------------------------------------------------------------------
+
+def test_ticks_closed_form():
+    # 1 mi at 60 mph = 60 s = 960 ticks; 1.5 mi at 45 mph = 120 s; 0.25 mi at 35 mph = 25.714 s
+    net = _single_path_net([1.0, 1.5, 0.25, 0.5, 0.875, 1e-6], 1)
+    sp = np.array([[60.0, 45.0, 35.0, 11520.0, 14400.0, 65.0]], np.float32)
+    t = net.day(sp).ticks()[0]
+    assert t[0] == 960 and t[1] == 1920
+    assert t[2] == 411                       # 411.43 rounds down
+    assert t[3] == 2                         # exactly 2.5 ticks: round half to even
+    assert t[4] == 4                         # exactly 3.5 ticks: round half to even
+    assert t[5] == 1                         # never below one tick
+
+
+@pytest.mark.parametrize("bad", [0.0, -5.0, np.nan, np.inf])
+def test_ticks_reject_bad_speed(bad):
+    net = _single_path_net([1.0], 2)
+    sp = np.array([[60.0], [bad]], np.float32)
+    with pytest.raises(orc.OracleError, match="rc=-4"):
+        net.day(sp)
+
+
+def test_ticks_overflow():
+    net = _single_path_net([1000.0], 1)
+    with pytest.raises(orc.OracleError, match="rc=-5"):
+        net.day(np.array([[1e-3]], np.float32))
+
+
+# ---------------------------------------------------------------------------
+# trajectories (Eq. (cost))
+# ---------------------------------------------------------------------------
+
+def test_trajectories_constant_speed_are_cumulative_sums():
+    # lengths m/64 mi at 60 mph take exactly 15 m ticks
+    m = np.array([64, 40, 96, 7, 128])
+    lengths = (m / 64.0).astype(np.float32)
+    N = 10
+    net = _single_path_net(lengths, N)
+    day = net.day(np.full((N, m.size), 60.0, np.float32))
+    T = day.trajectories()[0]
+    cum = np.concatenate([[0], np.cumsum(15 * m)])
+    expect = 4800 * np.arange(N + 1)[None, :] + cum[:, None]
+    np.testing.assert_array_equal(T, expect)
+    assert day.n_repairs == 0
+    C, p = day.route_choice()
+    # route time in minutes = sum(len)/60 mph * 60 min/h
+    np.testing.assert_allclose(C[:, 0], lengths.astype(np.float64).sum(), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(p, 1.0)
+
+
+def test_fifo_repair_and_point_mass():
+    # link 1 (2 mi) takes 10 mph in interval 0 (11520 ticks) and 64 mph afterwards
+    # (1800 ticks): the vehicle of boundary 1 would overtake the one of boundary 0.
+    N = 6
+    net = _single_path_net([2.0, 1.0], N)
+    sp = np.full((N, 2), 64.0, np.float32)
+    sp[0, 0] = 10.0
+    day = net.day(sp)
+    T = day.trajectories()[0]
+    assert day.n_repairs >= 1
+    assert T[1, 0] == 11520 and T[1, 1] == 11520          # repaired: no overtaking
+    assert np.all(np.diff(T, axis=1) >= 0)
+    kjh, rho = day.dar()
+    sel = (kjh[:, 0] == 0) & (kjh[:, 1] == 1) & (kjh[:, 2] == 0)
+    # zero-length window [11520, 11520): all mass in the interval containing it
+    np.testing.assert_array_equal(kjh[sel, 3], [11520 // 4800])
+    np.testing.assert_array_equal(rho[sel], [1.0])
+
+
+# ---------------------------------------------------------------------------
+# DAR (Eq. (dar)) -- paper's worked examples
+# ---------------------------------------------------------------------------
+
+def test_example_link_flow_path_flow():
+    g = _golden("example_link_path.json")
+    for case in g["cases"]:
+        m, phi = case["m"], case["phi"]
+        N = g["n_intervals"]
+        net = _single_path_net([case["link1_len_mi"], 1.0], N, g["interval_s"], g["ticks_per_s"])
+        day = net.day(np.full((N, 2), g["speed_mph"], np.float32))
+        kjh, rho = day.dar()
+        link2 = kjh[:, 1] == 1
+        for h1 in range(N):
+            sel = link2 & (kjh[:, 2] == h1)
+            got = dict(zip(kjh[sel, 3].tolist(), rho[sel].tolist()))
+            want = {}
+            if h1 + m < N:
+                want[h1 + m] = 1.0 - phi
+            if phi > 0 and h1 + m + 1 < N:
+                want[h1 + m + 1] = phi
+            want = {k: v for k, v in want.items() if v > 0}
+            assert got.keys() == want.keys(), (case, h1, got, want)
+            for k in want:
+                assert got[k] == pytest.approx(want[k], abs=1e-15)
+
+
+def test_example_dar_matrix_computation():
+    g = _golden("example_dar.json")
+    N = g["n_intervals"]
+    net = _single_path_net(g["link_len_mi"], N, g["interval_s"], g["ticks_per_s"])
+    day = net.day(np.asarray(g["speeds_mph_by_interval"], np.float32))
+    w = g["omega_ticks"]
+    env = {k: float(v) for k, v in w.items()}
+    kjh, rho = day.dar()
+    for j, name in enumerate(["link1", "link2", "link3"]):
+        sel = (kjh[:, 1] == j) & (kjh[:, 2] == 0)
+        got = dict(zip(kjh[sel, 3].tolist(), rho[sel].tolist()))
+        want = {int(h2): (float(v) if not isinstance(v, str) else eval(v, {}, env))
+                for h2, v in g["expected_h1_0"][name].items()}
+        assert got.keys() == want.keys(), (name, got, want)
+        for h2 in want:
+            assert got[h2] == pytest.approx(want[h2], abs=1e-15), (name, h2)
+    # the omegas themselves, from the trajectories (Sec. 2.4 relation)
+    T = day.trajectories()[0]
+    assert 4800 - T[1, 0] == w["omega1"] and T[1, 1] - 4800 == w["omega2"]
+    assert 4800 - T[2, 0] == w["omega3"] and T[2, 1] - 9600 == w["omega4"]
+
+
+def test_dar_partitions_each_departure():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    day = net.day(w.speeds([3])[0])
+    kjh, rho = day.dar()
+    trajs = day.trajectories()
+    # group sums over h2 for each (k, j, h1)
+    key = (kjh[:, 0].astype(np.int64) * 64 + kjh[:, 1]) * 1000 + kjh[:, 2]
+    uk, inv = np.unique(key, return_inverse=True)
+    sums = np.bincount(inv, weights=rho)
+    end = 4800 * w.n_intervals
+    checked_full = checked_cut = 0
+    for u, s in zip(uk, sums):
+        k, j, h1 = int(u // 1000 // 64), int(u // 1000 % 64), int(u % 1000)
+        lo, hi = trajs[k][j, h1], trajs[k][j, h1 + 1]
+        if hi <= end:
+            assert s == pytest.approx(1.0, abs=1e-14)
+            checked_full += 1
+        else:
+            assert s == pytest.approx((end - lo) / (hi - lo), abs=1e-14)   # mass after midnight dropped
+            checked_cut += 1
+    assert checked_full > 1000 and checked_cut > 0
+    # every (k, j, h1) whose window starts before midnight appears
+    n_expected = sum(int((trajs[k][:-1, :-1] < end).sum()) for k in range(len(trajs)))
+    assert uk.size == n_expected
+
+
+# ---------------------------------------------------------------------------
+# route choice (Eq. (logit))
+# ---------------------------------------------------------------------------
+
+def test_logit_properties():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    day = net.day(w.speeds([0])[0], theta=0.1)
+    C, p = day.route_choice()
+    od = w.routes.route_od
+    sums = np.zeros((w.n_intervals, w.routes.n_od))
+    for k in range(od.size):
+        sums[:, od[k]] += p[:, k]
+    np.testing.assert_allclose(sums, 1.0, atol=1e-15)
+    single = [k for k in range(od.size) if (od == od[k]).sum() == 1]
+    np.testing.assert_array_equal(p[:, single], 1.0)
+    # faster route gets the larger share, strictly
+    for k in range(od.size):
+        for k2 in range(od.size):
+            if k != k2 and od[k] == od[k2]:
+                faster = C[:, k] < C[:, k2]
+                assert np.all(p[faster, k] > p[faster, k2])
+    day.set_theta(0.0)
+    _, p0 = day.route_choice()
+    counts = np.bincount(od)
+    np.testing.assert_allclose(p0, np.broadcast_to(1.0 / counts[od][None, :], p0.shape), atol=1e-15)
+    day.set_theta(1e4)          # near-deterministic: all mass on the fastest route
+    _, pinf = day.route_choice()
+    for k in range(od.size):
+        if counts[od[k]] > 1:
+            others = [k2 for k2 in range(od.size) if od[k2] == od[k] and k2 != k]
+            fastest = np.all(C[:, [k]] < C[:, others] - 1e-3, axis=1)
+            np.testing.assert_allclose(pinf[fastest, k], 1.0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# forward / adjoint (Eq. (reverse), (flow), (assign))
+# ---------------------------------------------------------------------------
+
+def test_forward_constant_speed_is_a_two_tap_shift():
+    # every link at 60 mph, lengths m/64 mi -> delays 15 m ticks: link j of the
+    # path sees q shifted by D_j = (m_j + phi_j) intervals, split (1-phi, phi).
+    m = np.array([80, 320, 200, 64])          # 1200, 4800, 3000, 960 ticks
+    lengths = (m / 64.0).astype(np.float32)
+    N = 16
+    net = _single_path_net(lengths, N)
+    day = net.day(np.full((N, m.size), 60.0, np.float32))
+    rng = np.random.default_rng(0)
+    q = rng.gamma(2.0, 5.0, (N, 1))
+    x = day.forward(q)
+    delay = np.concatenate([[0], np.cumsum(15 * m)])[:-1]
+    for j in range(m.size):
+        whole, frac = divmod(int(delay[j]), 4800)
+        phi = frac / 4800.0
+        want = np.zeros(N)
+        for h1 in range(N):
+            if h1 + whole < N:
+                want[h1 + whole] += (1 - phi) * q[h1, 0]
+            if h1 + whole + 1 < N:
+                want[h1 + whole + 1] += phi * q[h1, 0]
+        np.testing.assert_allclose(x[:, j], want, rtol=1e-14, atol=1e-12)
+
+
+def test_forward_conserves_flow_and_adjoint_is_transpose():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    day = net.day(w.speeds([1])[0])
+    N, K, O = w.n_intervals, w.routes.n_od, w.net.n_obs
+    rng = np.random.default_rng(1)
+    q = rng.gamma(2.0, 5.0, (N, K))
+    q[N - 30:] = 0.0                     # nothing departs late enough to pass midnight
+    x = day.forward(q)
+    _, p = day.route_choice()
+    obs_col = {int(a): o for o, a in enumerate(w.net.obs_links)}
+    want = np.zeros(O)
+    for k in range(w.routes.n_routes):
+        f = p[:, k] * q[:, w.routes.route_od[k]]
+        for a in w.routes.links_of(k):
+            if int(a) in obs_col:
+                want[obs_col[int(a)]] += f.sum()
+    np.testing.assert_allclose(x.sum(axis=0), want, rtol=1e-12)
+    # <B q, r> = <q, B^T r>
+    r = rng.standard_normal((N, O))
+    g = day.adjoint(r)
+    lhs, rhs = float((x * r).sum()), float((q * g).sum())
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    # dense B agrees with both products (tiny slice of the day)
+    Bd = day.dense_B()
+    np.testing.assert_allclose(Bd @ q.ravel(), x.ravel(), rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(Bd.T @ r.ravel(), g.ravel(), rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# NNLS / SPGD (Eq. (nnls), Algorithm 1)
+# ---------------------------------------------------------------------------
+
+def _tiny_instance(noise=0.05, seed=3):
+    w = synth.tiny(n_intervals=4, interval_s=60, seed=seed)
+    net = orc.Net.from_workload(w)
+    sp = w.speeds([0])[0]
+    day = net.day(sp)
+    q_true = w.q_true([0])[0].astype(np.float64)
+    x_true = day.forward(q_true)
+    counts = (x_true * (1 + noise * w.noise_z([0])[0])).astype(np.float32)
+    return w, day, q_true, counts
+
+
+def test_tiny_instance_is_full_rank():
+    w, day, _, _ = _tiny_instance()
+    Bd = day.dense_B()
+    assert Bd.shape[1] == w.n_intervals * w.routes.n_od <= 14
+    assert np.linalg.matrix_rank(Bd) == Bd.shape[1]
+
+
+def test_exact_recovery_noise_free():
+    w, day, q_true, counts = _tiny_instance(noise=0.0)
+    mask = np.ones_like(counts, np.uint8)
+    q, G, loss = day.solve(counts, mask, iters=20000, eta=5.0)
+    np.testing.assert_allclose(q, q_true, rtol=1e-6, atol=1e-6)
+    assert loss < 1e-8
+
+
+def test_spgd_reaches_bruteforce_nnls_and_kkt():
+    # noisy counts and a negative-leaning target so that some constraints bind
+    w, day, q_true, counts = _tiny_instance(noise=0.3, seed=5)
+    Bd = day.dense_B()
+    counts = counts.copy()
+    counts[:, :2] -= 25.0
+    x = counts.astype(np.float64).ravel()
+    q_star = nnls_bruteforce(Bd, x)
+    assert np.any(q_star == 0) and np.any(q_star > 0)
+    mask = np.ones_like(counts, np.uint8)
+    q, G, loss = day.solve(counts, mask, iters=40000, eta=5.0)
+    np.testing.assert_allclose(q.ravel(), q_star, rtol=0, atol=1e-6 * max(1.0, np.abs(q_star).max()))
+    k = kkt_violation(Bd, x, q.ravel())
+    assert k["dual"] < 1e-8 and k["stationarity"] < 1e-8 and k["complementarity"] < 1e-8
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    q_ls, _ = scipy_opt.nnls(Bd, x)
+    np.testing.assert_allclose(q_star, q_ls, atol=1e-8)
+
+
+def test_masked_rows_do_not_count():
+    w, day, q_true, counts = _tiny_instance(noise=0.1)
+    mask = np.ones_like(counts, np.uint8)
+    mask[1, :] = 0
+    garbage = counts.copy()
+    garbage[1, :] = 1e6
+    a = day.solve(counts, mask, iters=50)
+    b = day.solve(garbage, mask, iters=50)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[2] == b[2]
+
+
+def test_row_chunk_covering_all_rows_equals_full_batch():
+    w, day, q_true, counts = _tiny_instance(noise=0.1)
+    mask = np.ones_like(counts, np.uint8)
+    full = day.solve(counts, mask, iters=30)
+    chunk = day.solve(counts, mask, iters=30, row_chunk=10_000, seed=9)
+    np.testing.assert_array_equal(full[0], chunk[0])
+
+
+def test_row_chunks_converge_to_nnls():
+    w, day, q_true, counts = _tiny_instance(noise=0.0)
+    mask = np.ones_like(counts, np.uint8)
+    q, G, loss = day.solve(counts, mask, iters=20000, row_chunk=5, seed=4)
+    np.testing.assert_allclose(q, q_true, rtol=1e-5, atol=1e-5)
+
+
+def test_day_order_does_not_change_per_day_results():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    days = [0, 1, 2]
+    sp, qt, z = w.speeds(days), w.q_true(days), w.noise_z(days)
+    x = net.forward_days(sp, qt)
+    counts = (x * (1 + 0.05 * z)).astype(np.float32)
+    mask = w.mask(days)
+    a = net.solve_days(sp, counts, mask, iters=5)
+    perm = [2, 0, 1]
+    b = net.solve_days(sp[perm], counts[perm], mask[perm], iters=5, n_threads=3)
+    for i, d in enumerate(perm):
+        np.testing.assert_array_equal(a[0][d], b[0][i])
+        assert a[2][d] == b[2][i]
+
+
+# ---------------------------------------------------------------------------
+# gradients of the differentiable form
+# ---------------------------------------------------------------------------
+
+def test_loss_grad_matches_central_differences():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    sp = w.speeds([2])[0]
+    day = net.day(sp, theta=0.1)
+    qt = w.q_true([2])[0].astype(np.float64)
+    counts = w.counts_from(day.forward(qt)[None], [2])[0]
+    mask = w.mask([2])[0]
+    rng = np.random.default_rng(7)
+    q = qt * rng.uniform(0.5, 1.5, qt.shape)
+    loss, dq, dth = day.loss_grad(counts, mask, q)
+    h = 1e-3
+    for (i, k) in [(100, 3), (200, 17), (80, 29), (10, 0)]:
+        qp, qm = q.copy(), q.copy()
+        qp[i, k] += h
+        qm[i, k] -= h
+        fd = (day.loss_grad(counts, mask, qp)[0] - day.loss_grad(counts, mask, qm)[0]) / (2 * h)
+        assert dq[i, k] == pytest.approx(fd, rel=1e-6, abs=1e-6)
+    def fd_theta(step):
+        day.set_theta(0.1 + step)
+        lp = day.loss_grad(counts, mask, q)[0]
+        day.set_theta(0.1 - step)
+        lm = day.loss_grad(counts, mask, q)[0]
+        return (lp - lm) / (2 * step)
+
+    # the loss is smooth but not quadratic in theta: central differences carry an
+    # O(h^2) error, so compare at h = 1e-3 loosely and after Richardson
+    # extrapolation (O(h^4)) tightly
+    d1, d2 = fd_theta(h), fd_theta(h / 2)
+    assert dth == pytest.approx(d1, rel=5e-4)
+    assert dth == pytest.approx((4 * d2 - d1) / 3, rel=1e-7)
+    assert abs(dth) > 0
+
+
+# ---------------------------------------------------------------------------
+# row order generator (Algorithm 1, permutate)
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_published_vectors():
+    g = _golden("splitmix64.json")
+    for s in g["sequences"]:
+        assert orc.splitmix64(s["seed"], len(s["outputs"])) == [int(v) for v in s["outputs"]]
+
+
+def test_permutation_is_uniform():
+    counts = {}
+    for e in range(6000):
+        p = tuple(orc.permute_rows(np.arange(3), seed=123, day=e % 7, epoch=e).tolist())
+        counts[p] = counts.get(p, 0) + 1
+    assert len(counts) == 6
+    vals = np.array(list(counts.values()), float)
+    chi2 = ((vals - 1000.0) ** 2 / 1000.0).sum()
+    assert chi2 < 20.5          # 5 dof, p ~ 0.001
+    big = orc.permute_rows(np.arange(1000), seed=5, day=3, epoch=2)
+    assert sorted(big.tolist()) == list(range(1000))
