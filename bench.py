@@ -1,0 +1,417 @@
+"""Benchmark of the per-day DODE SPGD solve (Ma & Qian, arXiv 1901.09266, Algorithm 1).
+
+One step = the whole hot path over the full synthetic workload: load the days
+(tick table, route times: ``dode_set_days``) and run ``--epochs`` SPGD epochs on
+every day (``dode_solve``).  Metric: SPGD day-iterations per second (one
+day-iteration = one full-row Adagrad update of one day), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Default workload: the 3-year corridor (1096 days x 288 five-minute intervals,
+150 OD pairs, 300 routes, 400 detectors, 10 % missing), 500 epochs per step,
+fused form with BF16 operands.  Inputs (~1.3 GB) exceed the 129 MB L2, and
+every step reloads them.  The plain FP32 form and the fused FP32 form are timed
+beside it at --compare-epochs epochs.
+
+Under torchrun (N > 1) each rank solves its own 1096 days (weak scaling, days
+d + 1096 * rank of the same generator); ranks exchange only the timing.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# algorithmic bytes of one day-iteration (DAR recomputed on chip, never stored):
+# counts 4 N O + bit mask N O / 8 + uint16 tick table 2 N A + q read+write
+# 8 N K + Adagrad accumulator read+write 8 N K + per-day loss 8
+def algorithmic_bytes(N: int, O: int, A: int, K: int) -> int:
+    return 4 * N * O + (N * O) // 8 + 2 * N * A + 8 * N * K + 8 * N * K + 8
+
+
+def shard_days(n_days: int, rank: int, world: int) -> list:
+    """Weak scaling: every rank owns a full set of n_days distinct days."""
+    return list(range(rank * n_days, (rank + 1) * n_days))
+
+
+def _peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines: list = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (torchrun); CPU-testable with gloo
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def dist_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def dist_max(x: float) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str, n_days: int):
+    from paper_1901_09266_gb300 import synth
+    if name == "corridor-3yr":
+        return synth.corridor_3yr(n_days=n_days)
+    if name == "corridor-uneven":
+        return synth.corridor_uneven(n_days=n_days)
+    if name == "corridor-large":
+        return synth.corridor_large(n_days=n_days)
+    if name == "corridor-7d":
+        return synth.corridor_7day()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def gpu_inputs(w, days):
+    """Speeds, noisy counts (B q_true with the library's own FP32 forward map) and mask."""
+    from paper_1901_09266_gb300 import dode
+    sp = w.speeds(days)
+    mask = w.mask(days)
+    qt = w.q_true(days)
+    ctx = dode.Context.from_workload(w)
+    ctx.set_days(np.zeros((len(days), w.n_intervals, w.net.n_obs), np.float32), sp, mask)
+    x = ctx.forward(qt)
+    ctx.close()
+    counts = w.counts_from(x, days)
+    return sp, counts, mask
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_rate(w, days, epochs: int, threads: int):
+    from oracle import oracle as orc
+    net = orc.Net.from_workload(w)
+    sp = w.speeds(days)
+    x = net.forward_days(sp, w.q_true(days).astype(np.float64), n_threads=threads)
+    counts = w.counts_from(x, days)
+    mask = w.mask(days)
+    t0 = time.perf_counter()
+    net.solve_days(sp, counts, mask, iters=epochs, eta=5.0, n_threads=threads, day_ids=np.asarray(days))
+    dt = time.perf_counter() - t0
+    return len(days) * epochs / dt, dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = make_workload(args.workload, args.days)
+    threads = os.cpu_count() or 1
+    days = list(range(min(args.ref_days, w.n_days)))
+    for _ in range(args.warmup):
+        oracle_rate(w, days[:threads], 1, threads)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = oracle_rate(w, days, args.ref_epochs, threads)
+        rates.append(r)
+        times.append(dt)
+    value = float(np.median(rates))
+    sample = f"{len(days)} days x {args.ref_epochs} epochs of {w.name} per step, FP64, OpenMP over days"
+    line = {
+        "impl": "reference", "metric": "SPGD day-iterations/sec", "value": value, "unit": "day-iter/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.median(times)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "days": w.n_days, "epochs_per_step": args.ref_epochs},
+        "cpu_baseline": {"value": value, "unit": "day-iter/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "day-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    from paper_1901_09266_gb300 import build, dode
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist_init("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    w = make_workload(args.workload, args.days)
+    days = shard_days(w.n_days, rank, world)
+    prec = dode.PREC_BF16 if args.precision == "bf16" else dode.PREC_FP32
+    form = dode.FORM_PLAIN if args.form == "plain" else dode.FORM_FUSED
+    ctx = dode.Context.from_workload(w, form=form, precision=prec)
+    ctx.use_torch_stream()
+    if args.block or args.ctas:
+        ctx.set_launch(args.block, args.ctas)
+    sp, counts, mask = gpu_inputs(w, days)
+    D, N, K, O, A = len(days), w.n_intervals, w.routes.n_od, w.net.n_obs, w.net.n_links
+    # device-resident inputs and outputs
+    sp_d = torch.from_numpy(sp).to(dev)
+    ct_d = torch.from_numpy(counts).to(dev)
+    mk_d = torch.from_numpy(mask).to(dev)
+    q_d = torch.empty((D, N, K), dtype=torch.float32, device=dev)
+    l_d = torch.empty(D, dtype=torch.float64, device=dev)
+    E = args.epochs
+
+    def step_device():
+        ctx.set_days(ct_d, sp_d, mk_d)
+        ctx.solve(E, args.step, args.batch, q_out=q_d, loss_out=l_d)
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    dist_barrier()
+    launches0 = ctx.total_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    dist_barrier()
+    e0.record()
+    kern_ms = []
+    for _ in range(args.steps):
+        step_device()
+        kern_ms.append(ctx.last_kernel_ms())
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    dist_barrier()
+    ms = e0.elapsed_time(e1)
+    ms = dist_max(ms)
+    launches = (ctx.total_launches() - launches0) // max(1, args.steps)
+    units = D * E * args.steps * world
+    value = units / (ms / 1e3)
+    final_loss = float(l_d.double().sum().item())
+
+    # end to end: pinned host buffers through the same calls
+    sp_h = torch.from_numpy(sp).pin_memory()
+    ct_h = torch.from_numpy(counts).pin_memory()
+    mk_h = torch.from_numpy(mask).pin_memory()
+    q_h = torch.empty((D, N, K), dtype=torch.float32).pin_memory()
+    l_h = torch.empty(D, dtype=torch.float64).pin_memory()
+    sp_n, ct_n, mk_n, q_n, l_n = sp_h.numpy(), ct_h.numpy(), mk_h.numpy(), q_h.numpy(), l_h.numpy()
+
+    def step_host():
+        ctx.set_days(ct_n, sp_n, mk_n)
+        ctx.solve(E, args.step, args.batch, q_out=q_n, loss_out=l_n)
+
+    e2e_value = None
+    if args.e2e_steps > 0:
+        step_host()
+        torch.cuda.synchronize()
+        dist_barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step_host()
+        torch.cuda.synchronize()
+        e2e_s = dist_max(time.perf_counter() - t0)
+        e2e_value = D * E * args.e2e_steps * world / e2e_s
+    h2d = sp.nbytes + counts.nbytes + mask.nbytes
+    d2h = q_n.nbytes + l_n.nbytes
+
+    # roofline of the fused kernel (algorithmic bytes / CUDA-event duration)
+    peaks = _peaks()
+    per_unit = algorithmic_bytes(N, O, A, K)
+    kms = float(np.mean(kern_ms))
+    achieved = per_unit * D * E / (kms / 1e3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak if peak else 6800.0, "unit": "GB/s",
+            "frac": achieved / (peak if peak else 6800.0), "traffic": args.traffic,
+            "peak_source": "measured" if peak else "fallback", "bytes_per_unit": per_unit,
+            "kernel_ms": kms}
+
+    # comparison forms at equal epochs from q = 0: plain FP32, fused FP32, and this form
+    forms = {}
+    if args.compare_epochs > 0 and rank == 0:
+        for name, fm, pr in [("plain_fp32", dode.FORM_PLAIN, dode.PREC_FP32),
+                             ("fused_fp32", dode.FORM_FUSED, dode.PREC_FP32),
+                             ("fused_bf16", dode.FORM_FUSED, dode.PREC_BF16)]:
+            c2 = dode.Context.from_workload(w, form=fm, precision=pr)
+            c2.use_torch_stream()
+            c2.set_days(ct_d, sp_d, mk_d)
+            c2.solve(1, args.step, args.batch, q_out=q_d, loss_out=l_d)          # warm-up (and plain DAR build)
+            c2.set_days(ct_d, sp_d, mk_d)
+            if fm == dode.FORM_PLAIN:
+                c2.solve(0, args.step, args.batch, q_out=q_d, loss_out=l_d)      # rebuild DAR outside the timing
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            c2.solve(args.compare_epochs, args.step, args.batch, q_out=q_d, loss_out=l_d)
+            b.record()
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b) / 1e3
+            forms[name] = {"day_iter_per_s": D * args.compare_epochs / t,
+                           "final_loss": float(l_d.double().sum().item()), "kernel_ms": c2.last_kernel_ms(),
+                           "launches": c2.last_launches()}
+            c2.close()
+        base = forms["plain_fp32"]
+        for v in forms.values():
+            v["speedup_vs_plain_fp32"] = v["day_iter_per_s"] / base["day_iter_per_s"]
+            v["final_loss_rel_diff_vs_plain"] = abs(v["final_loss"] - base["final_loss"]) / base["final_loss"]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        cd = list(range(min(args.ref_days, w.n_days)))
+        r, dt = oracle_rate(w, cd, args.ref_epochs, threads)
+        cpu = {"value": r, "unit": "day-iter/s", "cores": threads, "kind": "oracle",
+               "sample": f"{len(cd)} days x {args.ref_epochs} epochs of {w.name}, FP64, OpenMP over days ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": "SPGD day-iterations/sec", "value": value, "unit": "day-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == dode.PREC_BF16 else "f32", "data": "synthetic",
+            "config": {"workload": w.name, "days_per_gpu": D, "intervals": N, "od_pairs": K,
+                       "routes": w.routes.n_routes, "links": A, "detectors": O, "epochs_per_step": E,
+                       "form": args.form, "precision": args.precision,
+                       "l2": "inputs larger than L2 (reloaded every step)"},
+            "e2e": {"value": e2e_value, "unit": "day-iter/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "forms": forms,
+            "final_loss_total": final_loss,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="corridor-3yr")
+    ap.add_argument("--days", type=int, default=1096)
+    ap.add_argument("--epochs", type=int, default=500)
+    ap.add_argument("--step", type=float, default=5.0)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--form", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--compare-epochs", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-days", type=int, default=64)
+    ap.add_argument("--ref-epochs", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per fused launch from an ncu capture of the same kernel")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

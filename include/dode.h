@@ -1,0 +1,224 @@
+/*
+ * dode.h -- C ABI of libdode: per-day dynamic OD demand estimation (DODE) by
+ * stochastic projected gradient descent (SPGD) on GB300 (sm_103a).
+ *
+ * Method: Ma & Qian, "Estimating multi-year 24/7 origin-destination demand using
+ * high-granular multi-source traffic data" (arXiv 1901.09266).  For each day
+ * independently (Sec. 2.7) the library solves the NNLS problem of Eq. (opt) /
+ * Eq. (nnls):
+ *
+ *     min_{q >= 0}  sum_{a in A^o} sum_{h2} m[h2][a] (x[h2][a] - (B q)[h2][a])^2
+ *
+ * where B = delta * rho * p (Eq. (assign)) is rebuilt from the day's link speeds:
+ * link travel times (Sec. 2.4), leading-vehicle trajectories (Eq. (cost)), the
+ * dynamic assignment ratio rho (Eq. (dar)) and logit route choice (Eq. (logit)).
+ * Algorithm 1 (Sec. 3.3) with Adagrad and projection max(q, 0) is the solver.
+ *
+ * Conventions for every entry point:
+ *  - Return value: DODE_OK (0) or a negative DODE_ERR_* code.  No entry point
+ *    throws; dode_last_error() returns a message for the last failed call on a
+ *    context.
+ *  - Layouts are time-major as in the paper's Table "DODE framework variable
+ *    vectorization": q[d][h][od] (entry (h-1)|K| + od of day d), link arrays
+ *    x[d][h][o] with o the position of the link in dode_network.obs_links, speed
+ *    arrays [d][h][a] over all links.  All arrays are dense, C-contiguous.
+ *  - Pointer arguments tagged "ptr_kind" are host pointers (DODE_PTR_HOST) or
+ *    device pointers on the context's GPU (DODE_PTR_DEVICE); all others are host
+ *    pointers.  Inputs are borrowed only for the duration of the call (copied or
+ *    uploaded); outputs are caller-allocated.
+ *  - All device work is issued on the context's stream (dode_options.stream,
+ *    NULL = legacy default stream).  Every call returns after its work on that
+ *    stream has completed (device errors are reported by the call that caused
+ *    them).
+ *  - A context owns all its device memory.  Calls on one context are not
+ *    thread-safe; distinct contexts are independent.
+ *  - Time: ticks of 1/ticks_per_s s; an interval is interval_s * ticks_per_s
+ *    ticks (4800 for 5-minute intervals at 16 ticks/s).
+ */
+#ifndef DODE_H
+#define DODE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define DODE_OK 0
+#define DODE_ERR_ARG -1                  /* bad argument / size / pointer */
+#define DODE_ERR_ROUTE_NOT_CONTIGUOUS -2 /* head of link j != tail of link j+1 */
+#define DODE_ERR_ROUTE_REPEATS_LINK -3   /* a route uses a link twice (not a simple path) */
+#define DODE_ERR_BAD_SPEED -4            /* speed <= 0, NaN or Inf */
+#define DODE_ERR_TICK_OVERFLOW -5        /* a link travel time above 2^24 ticks */
+#define DODE_ERR_OOM -6                  /* device allocation failed */
+#define DODE_ERR_CUDA -7                 /* CUDA runtime error (message in dode_last_error) */
+#define DODE_ERR_DEVICE_TIMEOUT -8       /* a bounded device wait gave up */
+#define DODE_ERR_STATE -9                /* call order: e.g. solve before set_days */
+#define DODE_ERR_UNSUPPORTED -10         /* valid input this form does not handle */
+
+/* ---- enums ------------------------------------------------------------------ */
+#define DODE_PTR_HOST 0
+#define DODE_PTR_DEVICE 1
+
+#define DODE_FORM_FUSED 0  /* one persistent kernel, DAR recomputed on chip every pass */
+#define DODE_FORM_PLAIN 1  /* separate kernels over a DAR materialised in HBM */
+
+#define DODE_PREC_FP32 0   /* FP32 operands and accumulation */
+#define DODE_PREC_BF16 1   /* BF16 DAR fractions, demands and residuals; FP32 accumulation */
+
+#define DODE_MAX_ROUTE_LINKS 64
+
+/* ---- inputs ----------------------------------------------------------------- */
+
+/* Directed graph (Sec. 4, Step 0) and the observed link set A^o.            */
+typedef struct {
+    int32_t n_nodes;
+    int32_t n_links;
+    const int32_t *link_tail;   /* [n_links] node ids in [0, n_nodes) */
+    const int32_t *link_head;   /* [n_links] */
+    const float *link_len_mi;   /* [n_links] length in miles, finite, > 0 */
+    int32_t n_obs;              /* |A^o| >= 1 */
+    const int32_t *obs_links;   /* [n_obs] distinct link ids; column order of counts / mask */
+} dode_network;
+
+/* Path sets K_rs (Sec. 4, Step 0) in CSR form.                              */
+typedef struct {
+    int32_t n_od;               /* |K_q| */
+    int32_t n_routes;           /* Pi */
+    const int32_t *route_od;    /* [n_routes] OD pair of each route, in [0, n_od); every OD has >= 1 route */
+    const int32_t *route_ptr;   /* [n_routes + 1] offsets into route_links, route_ptr[0] = 0 */
+    const int32_t *route_links; /* links of route k in travel order, route_ptr[k] .. route_ptr[k+1]-1;
+                                   1 .. DODE_MAX_ROUTE_LINKS contiguous, distinct links */
+} dode_routes;
+
+typedef struct {
+    int32_t n_intervals;     /* N intervals per day (288) */
+    int32_t interval_s;      /* Delta H in seconds (300) */
+    int32_t ticks_per_s;     /* time resolution (16) */
+    float theta_per_min;     /* logit dispersion of Eq. (logit) on minutes (0.1); 0 = uniform split */
+    float eps;               /* Adagrad epsilon (1e-10) */
+    int32_t row_chunk;       /* Algorithm 1 batch size b in rows; 0 = all rows each update */
+    uint64_t seed;           /* row permutation seed (row_chunk > 0) */
+    int32_t form;            /* DODE_FORM_* */
+    int32_t precision;       /* DODE_PREC_* (fused form only) */
+    int32_t block_threads;   /* fused kernel CTA size (0 = tuned default) */
+    int32_t ctas_per_sm;     /* fused kernel CTAs per SM (0 = tuned default) */
+    int32_t device;          /* CUDA device ordinal (-1 = current) */
+    void *stream;            /* cudaStream_t for all work (NULL = default stream) */
+} dode_options;
+
+typedef struct dode_ctx dode_ctx;
+
+/* Fill *opt with the defaults listed above.                                   */
+void dode_default_options(dode_options *opt);
+
+/*
+ * dode_create -- validate the network and route sets and build a context.
+ * Network and routes are copied; the device copies of the route tables are
+ * built once here (OD-major route order, link -> observed column map).
+ * Errors: DODE_ERR_ARG (sizes, ids out of range, duplicated observed link, bad
+ * option), DODE_ERR_ROUTE_NOT_CONTIGUOUS, DODE_ERR_ROUTE_REPEATS_LINK,
+ * DODE_ERR_CUDA / DODE_ERR_OOM.  On error *out is NULL.
+ */
+int dode_create(const dode_network *net, const dode_routes *routes, const dode_options *opt,
+                dode_ctx **out);
+
+/*
+ * dode_set_days -- load D days of observations and speeds (Sec. 4, Steps 1 and 4).
+ *   counts [D][N][n_obs] link counts x (vehicles per interval), FP32
+ *   speeds [D][N][n_links] link speeds in mph (Sec. 2.4), FP32, finite, > 0
+ *   mask   [D][N][n_obs] 1 = observed, 0 = missing (excluded from the loss); NULL = all observed
+ * Computes the travel-time tick table and each day's route times once
+ * (Sec. 3.2 DAR construction inputs), and resets the solver state (q = 0,
+ * Adagrad accumulator = 0).  Errors: DODE_ERR_ARG, DODE_ERR_BAD_SPEED (first bad
+ * value reported in the message), DODE_ERR_TICK_OVERFLOW, DODE_ERR_OOM, DODE_ERR_CUDA.
+ */
+int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const float *speeds,
+                  const uint8_t *mask, int32_t ptr_kind);
+
+/* Replace the counts (and mask, if not NULL) of the loaded days; speeds and
+ * solver state are kept.  Same layouts as dode_set_days. */
+int dode_set_counts(dode_ctx *ctx, const float *counts, const uint8_t *mask, int32_t ptr_kind);
+
+/*
+ * dode_solve -- run `iters` epochs of Algorithm 1 (Sec. 3.3) on every loaded day,
+ * continuing from the current state (q, G), with step size `step` (eta, > 0).
+ *   batch     days per minibatch of the outer loop over days (>= 1, or 0 = all).
+ *             Days are independent problems (Sec. 2.7), so the minibatch order
+ *             changes no iterate; the device drains all days through one work
+ *             queue and runs each day's epochs back to back.
+ *   q_out     [D][N][n_od] final OD flows (ptr_kind), may be NULL
+ *   loss_out  [D] masked squared loss of the final q, FP64 (ptr_kind), may be NULL
+ * One epoch with row_chunk = 0 is one full-row update per day; with
+ * row_chunk = b > 0 the observed rows are permuted (SplitMix64 Fisher-Yates,
+ * state seed ^ (day << 32 | epoch)) and updated in chunks of b rows.
+ * Errors: DODE_ERR_STATE (no days loaded), DODE_ERR_ARG, DODE_ERR_UNSUPPORTED
+ * (row_chunk > 0 with the plain form), DODE_ERR_CUDA.
+ */
+int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q_out,
+               double *loss_out, int32_t ptr_kind);
+
+/* Per-epoch loss trace of the last dode_solve: trace[e][d] = masked loss of day d
+ * at the start of epoch e (FP32), host pointer [iters][D].  DODE_ERR_STATE if no
+ * solve has run since the days were loaded. */
+int dode_get_loss_trace(dode_ctx *ctx, float *trace, int32_t iters);
+
+/* Solver state: q and the Adagrad accumulator G, both [D][N][n_od] FP32.      */
+int dode_get_state(dode_ctx *ctx, float *q, float *G, int32_t ptr_kind);
+int dode_set_state(dode_ctx *ctx, const float *q, const float *G, int32_t ptr_kind);
+
+/* xhat[d][h][o] = (B_d q_d)[h][o], the link counts implied by q (Eq. (reverse)
+ * with Eq. (flow)); q [D][N][n_od], xhat [D][N][n_obs], same ptr_kind. */
+int dode_forward(dode_ctx *ctx, const float *q, float *xhat, int32_t ptr_kind);
+
+/*
+ * Differentiable form.  L(q, theta) = sum_d sum m (B_d(theta) q_d - x_d)^2 with
+ * the logit dispersion `theta` (per minute) in place of the context's.
+ *   loss   [D] per-day loss, FP64 (host)
+ *   dq     [D][N][n_od] dL/dq = 2 B^T r (ptr_kind), may be NULL
+ *   dtheta [D] dL/dtheta per day, FP64 (host), may be NULL
+ * The DAR is recomputed on the fly in both passes (nothing is checkpointed).
+ */
+int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t ptr_kind);
+int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, float *dq,
+                   double *dtheta, int32_t ptr_kind);
+
+/* ---- inspection (host outputs; for checks and debugging) --------------------- */
+
+/* Tick table of one day: out[h][a] = travel time of link a entered in interval h. */
+int dode_get_ticks(dode_ctx *ctx, int32_t day, int32_t *out);
+/* Route times of one day in minutes: out[h][k] (Eq. (cost)), leading vehicle of t^h. */
+int dode_get_route_times(dode_ctx *ctx, int32_t day, float *out);
+/* FIFO repairs applied on one day and the largest trip offset in intervals. */
+int dode_get_day_info(dode_ctx *ctx, int32_t day, int64_t *n_repairs, int32_t *max_offset);
+/*
+ * DAR entries of one day for every (route k, link position j, departure h1)
+ * (Eq. (dar)), as built by the plain form's DAR builder.  Call with kjh = rho =
+ * NULL to get the count in *n; then with arrays of that size:
+ *   kjh [n][4] = (k, j, h1, h2), rho [n] FP32, ordered by (k, j, h1, h2).
+ */
+int dode_get_dar(dode_ctx *ctx, int32_t day, int64_t *n, int32_t *kjh, float *rho);
+
+/* ---- timing and launch shape --------------------------------------------------- */
+
+/* Device time in ms of the hot-path kernel(s) of the last solve / forward / loss
+ * call, measured with CUDA events on the context's stream. */
+double dode_last_kernel_ms(const dode_ctx *ctx);
+/* Number of hot-path kernel launches the last solve / forward / loss call made. */
+int64_t dode_last_launches(const dode_ctx *ctx);
+/* Number of kernel launches (all kernels, all calls) made by this context so far. */
+int64_t dode_total_launches(const dode_ctx *ctx);
+/* Override the fused kernel launch shape (autotuner); 0 = tuned default. */
+int dode_set_launch(dode_ctx *ctx, int32_t block_threads, int32_t ctas_per_sm);
+/* Switch stream (cudaStream_t); the context's previous work must be complete. */
+int dode_set_stream(dode_ctx *ctx, void *stream);
+
+const char *dode_last_error(const dode_ctx *ctx);
+void dode_destroy(dode_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DODE_H */

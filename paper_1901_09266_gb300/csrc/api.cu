@@ -1,0 +1,1077 @@
+// api.cu -- host implementation of the C ABI declared in include/dode.h.
+//
+// The context owns every device buffer (cudaMalloc'd once per size change) and
+// issues all work on its stream.  Inputs in the ABI's time-major layouts are
+// converted to the kernels' time-innermost layouts on entry (dode_internal.cuh)
+// and results converted back on exit.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/dode.h"
+#include "dode_internal.cuh"
+
+using namespace dode;
+
+struct dode_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int n_sm = 0;
+    size_t smem_optin = 0;
+    dode_options opt{};
+    int N = 0, Np = 0, Nw = 0, ipt = 0, tps = 0, A = 0, O = 0, Ow = 0, K = 0, P = 0, L = 0;
+    IntervalDiv div{};
+    std::vector<int32_t> rptr, rlinks, rod, obs, obs_col, od_ptr, od_routes, task_od;
+    std::vector<float> len;
+    std::vector<int32_t> pair_k, pair_j, pair_o, rpp;  // observed (route, position) pairs
+    std::vector<int2> rpack;                           // (link, observed column) per route position
+    int2 *d_rpack = nullptr;
+    float *d_pt = nullptr;                             // route choice table [D][P][Np]
+    int32_t *d_rptr = nullptr, *d_rlinks = nullptr, *d_rod = nullptr, *d_obs_col = nullptr, *d_od_ptr = nullptr,
+            *d_od_routes = nullptr, *d_task_od = nullptr;
+    int32_t *d_pair_k = nullptr, *d_pair_j = nullptr, *d_pair_o = nullptr, *d_rpp = nullptr;
+    float *d_len = nullptr;
+    // days
+    int D = 0;
+    int32_t *d_ticks = nullptr;
+    float *d_counts = nullptr;
+    uint32_t *d_mask = nullptr, *d_colact = nullptr;
+    float *d_C = nullptr;
+    int32_t *d_maxoff = nullptr;
+    unsigned long long *d_repairs = nullptr;
+    int64_t *d_tab_off = nullptr;
+    int32_t *d_traj_tab = nullptr;
+    std::vector<int32_t> h_maxoff;
+    std::vector<unsigned long long> h_repairs;
+    int maxoff_max = 0;
+    int max_tick = 0;
+    float *d_q = nullptr, *d_G = nullptr, *d_qtmp = nullptr, *d_gout = nullptr, *d_xout = nullptr;
+    __nv_bfloat16 *d_qb = nullptr;
+    double *d_loss = nullptr, *d_dtheta = nullptr;
+    float *d_trace = nullptr;
+    size_t trace_cap = 0;
+    int trace_iters = -1;
+    void *d_rbuf = nullptr;
+    size_t rbuf_bytes = 0;
+    float *d_gring = nullptr;
+    size_t gring_bytes = 0;
+    int *d_queue = nullptr, *d_err = nullptr;
+    void *d_stage = nullptr;
+    size_t stage_bytes = 0;
+    // plain form
+    int4 *d_rec = nullptr;
+    float *d_p = nullptr;
+    double *d_ptrace = nullptr;
+    size_t ptrace_cap = 0;
+    bool plain_ready = false;
+    // timing
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = 0.0;
+    int64_t last_launches = 0;
+    int64_t total_launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(dode_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CU(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            int code_ = (e_ == cudaErrorMemoryAllocation) ? DODE_ERR_OOM : DODE_ERR_CUDA;        \
+            return fail(ctx, code_, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                        \
+    } while (0)
+
+// a kernel launch: checked and counted
+#define CUL(call)                  \
+    do {                           \
+        CU(call);                  \
+        ++ctx->total_launches;     \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+template <class T>
+cudaError_t upload(T **d, const std::vector<T> &h, cudaStream_t s) {
+    cudaError_t e = dalloc(d, h.size());
+    if (e != cudaSuccess) return e;
+    if (h.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+int set_device(dode_ctx *ctx) {
+    CU(cudaSetDevice(ctx->dev));
+    return DODE_OK;
+}
+
+// Staging buffer on the device for host <-> device copies in ABI layout.
+int stage(dode_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->stage_bytes) return DODE_OK;
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_bytes = 0;
+    CU(cudaMalloc(&ctx->d_stage, bytes));
+    ctx->stage_bytes = bytes;
+    return DODE_OK;
+}
+
+int check_device_error(dode_ctx *ctx) {
+    int h[3] = {0, 0, 0};
+    CU(cudaMemcpyAsync(h, ctx->d_err, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (h[0] == 0) return DODE_OK;
+    long long idx = (long long)(uint32_t)h[1] | ((long long)h[2] << 31);
+    char buf[256];
+    if (h[0] == DODE_ERR_BAD_SPEED || h[0] == DODE_ERR_TICK_OVERFLOW) {
+        long long a = idx % ctx->A, dh = idx / ctx->A;
+        snprintf(buf, sizeof buf, "%s at day %lld, interval %lld, link %lld",
+                 h[0] == DODE_ERR_BAD_SPEED ? "speed not finite and positive" : "link travel time above 2^24 ticks",
+                 dh / ctx->N, dh % ctx->N, a);
+    } else if (h[0] == DODE_ERR_UNSUPPORTED) {
+        snprintf(buf, sizeof buf, "unsupported input at item %lld (window spans more intervals than this form handles)", idx);
+    } else {
+        snprintf(buf, sizeof buf, "device error %d at item %lld", h[0], idx);
+    }
+    CU(cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));
+    return fail(ctx, h[0], buf);
+}
+
+bool bad_ptr_kind(int k) { return k != DODE_PTR_HOST && k != DODE_PTR_DEVICE; }
+
+// Copy an ABI-layout input to the device (no-op for device pointers).
+int input(dode_ctx *ctx, const void *src, size_t bytes, int ptr_kind, size_t stage_off, const void **dev) {
+    if (ptr_kind == DODE_PTR_DEVICE) {
+        *dev = src;
+        return DODE_OK;
+    }
+    char *dst = static_cast<char *>(ctx->d_stage) + stage_off;
+    CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *dev = dst;
+    return DODE_OK;
+}
+
+// [D][K][Np] internal -> [D][N][K] caller buffer.
+int output_odmajor(dode_ctx *ctx, const float *src, float *dst, int M, float scale, int ptr_kind) {
+    const size_t bytes = (size_t)ctx->D * ctx->N * M * sizeof(float);
+    float *tgt = dst;
+    if (ptr_kind == DODE_PTR_HOST) {
+        int rc = stage(ctx, bytes);
+        if (rc) return rc;
+        tgt = static_cast<float *>(ctx->d_stage);
+    }
+    CUL(launch_transpose_out(src, tgt, ctx->D, ctx->N, ctx->Np, M, scale, ctx->stream));
+    if (ptr_kind == DODE_PTR_HOST) CU(cudaMemcpyAsync(dst, tgt, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return DODE_OK;
+}
+
+// [D][N][M] caller -> [D][M][Np] internal.
+int input_odmajor(dode_ctx *ctx, const float *src, float *dst, int M, int ptr_kind) {
+    const size_t bytes = (size_t)ctx->D * ctx->N * M * sizeof(float);
+    const void *dsrc = src;
+    if (ptr_kind == DODE_PTR_HOST) {
+        int rc = stage(ctx, bytes);
+        if (rc) return rc;
+        rc = input(ctx, src, bytes, ptr_kind, 0, &dsrc);
+        if (rc) return rc;
+    }
+    CUL(launch_transpose_in(static_cast<const float *>(dsrc), dst, ctx->D, ctx->N, ctx->Np, M, ctx->stream));
+    return DODE_OK;
+}
+
+int output_plain(dode_ctx *ctx, const void *src, void *dst, size_t bytes, int ptr_kind) {
+    CU(cudaMemcpyAsync(dst, src, bytes,
+                       ptr_kind == DODE_PTR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream));
+    return DODE_OK;
+}
+
+struct FusedShape {
+    int block, grid, ring_rows, tick_rows, tiles_per_phase;
+    size_t smem;
+};
+
+// Launch shape of the fused kernel: CTA size, CTAs per SM and the shared-memory
+// windows.  A phase of F tiles needs R = 31 F + maxoff + 2 ring rows per
+// observed link (FP32) and RW = 31 F + maxoff + 1 tick rows per link (uint16,
+// only when every tick fits 16 bits).  The largest F up to 3 that fits is
+// taken; otherwise ticks are read from global memory, and if even the ring
+// does not fit the link flows accumulate in global memory.
+int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
+    const int ntiles = (ctx->N + kTileW - 1) / kTileW;
+    const int per_sm = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 1;
+    int block = ctx->opt.block_threads > 0 ? ctx->opt.block_threads : (per_sm == 1 ? 1024 : 512);
+    block = std::max(32, std::min(1024, block / 32 * 32));
+    const size_t reserve = 2048;
+    size_t budget = std::min<size_t>(ctx->smem_optin, (size_t)(228 * 1024) / per_sm - 1024);
+    budget = budget > reserve ? budget - reserve : 0;
+    const size_t colact = ((size_t)ctx->Ow * sizeof(uint32_t) + 15) & ~(size_t)15;
+    const bool ticks16 = ctx->max_tick <= 65535;
+    const int mo = ctx->maxoff_max;
+    int R = 0, RW = 0, F = 0;
+    for (int f = std::min(3, ntiles); f >= 1 && F == 0; --f) {
+        const size_t ring = (size_t)ctx->O * (kTileW * f + mo + 2) * sizeof(float);
+        const size_t tw = ticks16 ? (size_t)ctx->A * (kTileW * f + mo + 1) * sizeof(uint16_t) : (size_t)-1;
+        if (ticks16 && ring + colact + tw <= budget) {
+            F = f;
+            R = kTileW * f + mo + 2;
+            RW = kTileW * f + mo + 1;
+        }
+    }
+    for (int f = std::min(3, ntiles); f >= 1 && F == 0; --f) {
+        const size_t ring = (size_t)ctx->O * (kTileW * f + mo + 2) * sizeof(float);
+        if (ring + colact <= budget) {
+            F = f;
+            R = kTileW * f + mo + 2;
+        }
+    }
+    if (F == 0) F = ntiles;
+    const size_t smem = (R ? (size_t)ctx->O * R * sizeof(float) : 0) + colact + (RW ? (size_t)ctx->A * RW * 2 : 0);
+    int occ = 0;
+    cudaError_t e = fused_occupancy(precision, block, smem, &occ);
+    if (e != cudaSuccess) return fail(ctx, DODE_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+    if (occ < 1) return fail(ctx, DODE_ERR_UNSUPPORTED, "fused kernel launch shape does not fit on an SM");
+    occ = std::min(occ, per_sm);
+    s->block = block;
+    s->grid = std::max(1, std::min(ctx->D, ctx->n_sm * occ));
+    s->ring_rows = R;
+    s->tick_rows = RW;
+    s->tiles_per_phase = F;
+    s->smem = smem;
+    return DODE_OK;
+}
+
+int ensure_slots(dode_ctx *ctx, const FusedShape &s, int precision) {
+    const size_t elems = (size_t)s.grid * ctx->O * ctx->Np;
+    const size_t rb = elems * (precision == DODE_PREC_BF16 ? 2 : 4);
+    if (rb > ctx->rbuf_bytes) {
+        if (ctx->d_rbuf) cudaFree(ctx->d_rbuf);
+        ctx->d_rbuf = nullptr;
+        ctx->rbuf_bytes = 0;
+        CU(cudaMalloc(&ctx->d_rbuf, rb));
+        ctx->rbuf_bytes = rb;
+    }
+    if (s.ring_rows == 0 && elems * 4 > ctx->gring_bytes) {
+        dfree(ctx->d_gring);
+        ctx->gring_bytes = 0;
+        CU(cudaMalloc(&ctx->d_gring, elems * 4));
+        ctx->gring_bytes = elems * 4;
+    }
+    return DODE_OK;
+}
+
+FusedParams base_params(dode_ctx *ctx) {
+    FusedParams p{};
+    p.N = ctx->N;
+    p.Np = ctx->Np;
+    p.Nw = ctx->Nw;
+    p.A = ctx->A;
+    p.O = ctx->O;
+    p.Ow = ctx->Ow;
+    p.K = ctx->K;
+    p.P = ctx->P;
+    p.div = ctx->div;
+    p.rptr = ctx->d_rptr;
+    p.rlinks = ctx->d_rlinks;
+    p.obs_col = ctx->d_obs_col;
+    p.od_ptr = ctx->d_od_ptr;
+    p.od_routes = ctx->d_od_routes;
+    p.task_od = ctx->d_task_od;
+    p.rpack = ctx->d_rpack;
+    p.pt = ctx->d_pt;
+    p.ticks = ctx->d_ticks;
+    p.counts = ctx->d_counts;
+    p.mask = ctx->d_mask;
+    p.colact = ctx->d_colact;
+    p.C = ctx->d_C;
+    p.maxoff = ctx->d_maxoff;
+    p.tab_off = ctx->d_tab_off;
+    p.traj_tab = ctx->d_traj_tab;
+    p.q = ctx->d_q;
+    p.G = ctx->d_G;
+    p.qb = ctx->d_qb;
+    p.loss = ctx->d_loss;
+    p.dtheta = ctx->d_dtheta;
+    p.n_days = ctx->D;
+    p.eps = ctx->opt.eps;
+    p.theta = ctx->opt.theta_per_min;
+    p.queue = ctx->d_queue;
+    p.err = ctx->d_err;
+    return p;
+}
+
+int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
+    FusedShape s;
+    int rc = fused_shape(ctx, precision, &s);
+    if (rc) return rc;
+    rc = ensure_slots(ctx, s, precision);
+    if (rc) return rc;
+    p.rbuf = ctx->d_rbuf;
+    p.gring = ctx->d_gring;
+    p.ring_rows = s.ring_rows;
+    p.tick_rows = s.tick_rows;
+    p.tiles_per_phase = s.tiles_per_phase;
+    CUL(launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, ctx->D, ctx->P, ctx->N,
+                            ctx->Np, ctx->d_pt, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    CUL(launch_fused(p, precision, s.grid, s.block, s.smem, ctx->stream));
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    ctx->last_launches = 1;
+    return DODE_OK;
+}
+
+int finish_timing(dode_ctx *ctx) {
+    CU(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->last_ms = ms;
+    return DODE_OK;
+}
+
+void free_days(dode_ctx *ctx) {
+    dfree(ctx->d_ticks);
+    dfree(ctx->d_counts);
+    dfree(ctx->d_mask);
+    dfree(ctx->d_colact);
+    dfree(ctx->d_C);
+    dfree(ctx->d_pt);
+    dfree(ctx->d_maxoff);
+    dfree(ctx->d_repairs);
+    dfree(ctx->d_tab_off);
+    dfree(ctx->d_traj_tab);
+    dfree(ctx->d_q);
+    dfree(ctx->d_G);
+    dfree(ctx->d_qb);
+    dfree(ctx->d_qtmp);
+    dfree(ctx->d_gout);
+    dfree(ctx->d_xout);
+    dfree(ctx->d_loss);
+    dfree(ctx->d_dtheta);
+    dfree(ctx->d_trace);
+    ctx->trace_cap = 0;
+    dfree(ctx->d_rec);
+    dfree(ctx->d_p);
+    dfree(ctx->d_ptrace);
+    ctx->ptrace_cap = 0;
+    ctx->plain_ready = false;
+    ctx->D = 0;
+}
+
+// Plain form: build DAR records (all days) and route choice for theta.
+int plain_prepare(dode_ctx *ctx, float theta, PlainParams *pp) {
+    PlainParams p{};
+    p.N = ctx->N;
+    p.Np = ctx->Np;
+    p.Nw = ctx->Nw;
+    p.A = ctx->A;
+    p.O = ctx->O;
+    p.K = ctx->K;
+    p.P = ctx->P;
+    p.n_pairs = (int)ctx->pair_k.size();
+    p.div = ctx->div;
+    p.rptr = ctx->d_rptr;
+    p.rlinks = ctx->d_rlinks;
+    p.rod = ctx->d_rod;
+    p.od_ptr = ctx->d_od_ptr;
+    p.od_routes = ctx->d_od_routes;
+    p.pair_k = ctx->d_pair_k;
+    p.pair_j = ctx->d_pair_j;
+    p.pair_o = ctx->d_pair_o;
+    p.route_pair_ptr = ctx->d_rpp;
+    p.ticks = ctx->d_ticks;
+    p.tab_off = ctx->d_tab_off;
+    p.traj_tab = ctx->d_traj_tab;
+    p.C = ctx->d_C;
+    p.theta = theta;
+    p.n_days = ctx->D;
+    p.err = ctx->d_err;
+    if (!ctx->plain_ready) {
+        CU(dalloc(&ctx->d_rec, (size_t)ctx->D * p.n_pairs * ctx->N));
+        CU(dalloc(&ctx->d_p, (size_t)ctx->D * ctx->P * ctx->Np));
+    }
+    p.rec = ctx->d_rec;
+    p.p = ctx->d_p;
+    if (!ctx->plain_ready) {
+        CUL(launch_plain_build(p, ctx->stream));
+        int rc = check_device_error(ctx);
+        if (rc) return rc;
+        ctx->plain_ready = true;
+    }
+    CUL(launch_plain_route_choice(p, ctx->stream));
+    *pp = p;
+    return DODE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dode_default_options(dode_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->n_intervals = 288;
+    o->interval_s = 300;
+    o->ticks_per_s = 16;
+    o->theta_per_min = 0.1f;
+    o->eps = 1e-10f;
+    o->row_chunk = 0;
+    o->seed = 0;
+    o->form = DODE_FORM_FUSED;
+    o->precision = DODE_PREC_FP32;
+    o->block_threads = 0;
+    o->ctas_per_sm = 0;
+    o->device = -1;
+    o->stream = nullptr;
+}
+
+const char *dode_last_error(const dode_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+double dode_last_kernel_ms(const dode_ctx *ctx) { return ctx ? ctx->last_ms : 0.0; }
+
+int64_t dode_last_launches(const dode_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+int64_t dode_total_launches(const dode_ctx *ctx) { return ctx ? ctx->total_launches : 0; }
+
+int dode_create(const dode_network *net, const dode_routes *routes, const dode_options *opt, dode_ctx **out) {
+    if (!out) return DODE_ERR_ARG;
+    *out = nullptr;
+    if (!net || !routes) return DODE_ERR_ARG;
+    dode_options o;
+    if (opt)
+        o = *opt;
+    else
+        dode_default_options(&o);
+    dode_ctx *ctx = new dode_ctx();
+    auto bail = [&](int code, const std::string &m) {
+        static thread_local std::string last;
+        last = m;
+        delete ctx;
+        fprintf(stderr, "dode_create: %s\n", m.c_str());
+        return code;
+    };
+    if (net->n_nodes < 1 || net->n_links < 1 || net->n_obs < 1 || !net->link_tail || !net->link_head ||
+        !net->link_len_mi || !net->obs_links)
+        return bail(DODE_ERR_ARG, "network sizes / pointers");
+    if (routes->n_od < 1 || routes->n_routes < 1 || !routes->route_od || !routes->route_ptr || !routes->route_links)
+        return bail(DODE_ERR_ARG, "route sizes / pointers");
+    if (o.n_intervals < 1 || o.interval_s < 1 || o.ticks_per_s < 1 || !std::isfinite(o.theta_per_min) ||
+        !(o.eps >= 0.f) || o.row_chunk < 0 || (o.form != DODE_FORM_FUSED && o.form != DODE_FORM_PLAIN) ||
+        (o.precision != DODE_PREC_FP32 && o.precision != DODE_PREC_BF16) || o.block_threads < 0 || o.ctas_per_sm < 0)
+        return bail(DODE_ERR_ARG, "options");
+    const long long ipt = (long long)o.interval_s * o.ticks_per_s;
+    if (ipt < 2 || ipt > (1 << 24) || ipt * o.n_intervals > (1LL << 29))
+        return bail(DODE_ERR_ARG, "interval of 2 .. 2^24 ticks and a day of at most 2^29 ticks");
+    const int A = net->n_links, O = net->n_obs, K = routes->n_od, P = routes->n_routes;
+    for (int a = 0; a < A; ++a) {
+        if (net->link_tail[a] < 0 || net->link_tail[a] >= net->n_nodes || net->link_head[a] < 0 ||
+            net->link_head[a] >= net->n_nodes)
+            return bail(DODE_ERR_ARG, "link endpoint out of range at link " + std::to_string(a));
+        if (!(net->link_len_mi[a] > 0.f) || !std::isfinite(net->link_len_mi[a]))
+            return bail(DODE_ERR_ARG, "link length not finite and positive at link " + std::to_string(a));
+    }
+    std::vector<int32_t> obs_col(A, -1);
+    for (int i = 0; i < O; ++i) {
+        int a = net->obs_links[i];
+        if (a < 0 || a >= A) return bail(DODE_ERR_ARG, "observed link id out of range");
+        if (obs_col[a] >= 0) return bail(DODE_ERR_ARG, "observed link listed twice: " + std::to_string(a));
+        obs_col[a] = i;
+    }
+    if (routes->route_ptr[0] != 0) return bail(DODE_ERR_ARG, "route_ptr[0] != 0");
+    std::vector<int> od_count(K, 0);
+    for (int k = 0; k < P; ++k) {
+        const int od = routes->route_od[k];
+        if (od < 0 || od >= K) return bail(DODE_ERR_ARG, "route_od out of range at route " + std::to_string(k));
+        ++od_count[od];
+        const int l0 = routes->route_ptr[k], l1 = routes->route_ptr[k + 1];
+        if (l1 - l0 < 1 || l1 - l0 > DODE_MAX_ROUTE_LINKS)
+            return bail(DODE_ERR_ARG, "route length outside 1..64 at route " + std::to_string(k));
+        for (int j = l0; j < l1; ++j) {
+            const int a = routes->route_links[j];
+            if (a < 0 || a >= A) return bail(DODE_ERR_ARG, "route link out of range at route " + std::to_string(k));
+            if (j + 1 < l1 && net->link_head[a] != net->link_tail[routes->route_links[j + 1]])
+                return bail(DODE_ERR_ROUTE_NOT_CONTIGUOUS, "route " + std::to_string(k) + " not contiguous");
+            for (int i = l0; i < j; ++i)
+                if (routes->route_links[i] == a)
+                    return bail(DODE_ERR_ROUTE_REPEATS_LINK, "route " + std::to_string(k) + " repeats a link");
+        }
+    }
+    for (int od = 0; od < K; ++od)
+        if (od_count[od] == 0) return bail(DODE_ERR_ARG, "OD pair without a route: " + std::to_string(od));
+
+    ctx->opt = o;
+    ctx->N = o.n_intervals;
+    ctx->Np = (o.n_intervals + 1 + 31) / 32 * 32;
+    ctx->Nw = (o.n_intervals + 31) / 32;
+    ctx->ipt = (int)ipt;
+    ctx->tps = o.ticks_per_s;
+    ctx->div = make_interval_div((int)ipt);
+    ctx->A = A;
+    ctx->O = O;
+    ctx->Ow = (O + 31) / 32;
+    ctx->K = K;
+    ctx->P = P;
+    ctx->L = routes->route_ptr[P];
+    ctx->rptr.assign(routes->route_ptr, routes->route_ptr + P + 1);
+    ctx->rlinks.assign(routes->route_links, routes->route_links + ctx->L);
+    ctx->rod.assign(routes->route_od, routes->route_od + P);
+    ctx->obs.assign(net->obs_links, net->obs_links + O);
+    ctx->obs_col = obs_col;
+    ctx->len.assign(net->link_len_mi, net->link_len_mi + A);
+    // OD-major route order and OD tasks, largest walk first
+    ctx->od_ptr.assign(K + 1, 0);
+    for (int k = 0; k < P; ++k) ++ctx->od_ptr[ctx->rod[k] + 1];
+    for (int od = 0; od < K; ++od) ctx->od_ptr[od + 1] += ctx->od_ptr[od];
+    ctx->od_routes.assign(P, 0);
+    {
+        std::vector<int> fill(ctx->od_ptr.begin(), ctx->od_ptr.end() - 1);
+        for (int k = 0; k < P; ++k) ctx->od_routes[fill[ctx->rod[k]]++] = k;
+    }
+    std::vector<long long> work(K, 0);
+    for (int k = 0; k < P; ++k) work[ctx->rod[k]] += ctx->rptr[k + 1] - ctx->rptr[k];
+    ctx->task_od.resize(K);
+    std::iota(ctx->task_od.begin(), ctx->task_od.end(), 0);
+    std::stable_sort(ctx->task_od.begin(), ctx->task_od.end(), [&](int a, int b) { return work[a] > work[b]; });
+    ctx->rpack.resize(ctx->L);
+    for (int j = 0; j < ctx->L; ++j) ctx->rpack[j] = make_int2(ctx->rlinks[j], obs_col[ctx->rlinks[j]]);
+    // observed (route, position) pairs for the plain form
+    ctx->rpp.assign(P + 1, 0);
+    for (int k = 0; k < P; ++k) {
+        for (int j = ctx->rptr[k]; j < ctx->rptr[k + 1]; ++j) {
+            const int o2 = obs_col[ctx->rlinks[j]];
+            if (o2 < 0) continue;
+            ctx->pair_k.push_back(k);
+            ctx->pair_j.push_back(j - ctx->rptr[k]);
+            ctx->pair_o.push_back(o2);
+        }
+        ctx->rpp[k + 1] = (int32_t)ctx->pair_k.size();
+    }
+
+    if (o.device >= 0) {
+        if (cudaSetDevice(o.device) != cudaSuccess) return bail(DODE_ERR_CUDA, "cudaSetDevice");
+    }
+    if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(DODE_ERR_CUDA, "no CUDA device");
+    ctx->stream = static_cast<cudaStream_t>(o.stream);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->dev) != cudaSuccess) return bail(DODE_ERR_CUDA, "device properties");
+    ctx->n_sm = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+#define CUB(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return bail(DODE_ERR_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+    CUB(upload(&ctx->d_rptr, ctx->rptr, ctx->stream));
+    CUB(upload(&ctx->d_rlinks, ctx->rlinks, ctx->stream));
+    CUB(upload(&ctx->d_rod, ctx->rod, ctx->stream));
+    CUB(upload(&ctx->d_obs_col, ctx->obs_col, ctx->stream));
+    CUB(upload(&ctx->d_od_ptr, ctx->od_ptr, ctx->stream));
+    CUB(upload(&ctx->d_od_routes, ctx->od_routes, ctx->stream));
+    CUB(upload(&ctx->d_task_od, ctx->task_od, ctx->stream));
+    CUB(upload(&ctx->d_pair_k, ctx->pair_k, ctx->stream));
+    CUB(upload(&ctx->d_pair_j, ctx->pair_j, ctx->stream));
+    CUB(upload(&ctx->d_pair_o, ctx->pair_o, ctx->stream));
+    CUB(upload(&ctx->d_rpp, ctx->rpp, ctx->stream));
+    CUB(upload(&ctx->d_len, ctx->len, ctx->stream));
+    CUB(upload(&ctx->d_rpack, ctx->rpack, ctx->stream));
+    CUB(cudaMalloc(&ctx->d_queue, sizeof(int)));
+    CUB(cudaMalloc(&ctx->d_err, 4 * sizeof(int)));
+    CUB(cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));
+    CUB(cudaEventCreate(&ctx->ev0));
+    CUB(cudaEventCreate(&ctx->ev1));
+    CUB(cudaStreamSynchronize(ctx->stream));
+#undef CUB
+    *out = ctx;
+    return DODE_OK;
+}
+
+void dode_destroy(dode_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    free_days(ctx);
+    dfree(ctx->d_rptr);
+    dfree(ctx->d_rlinks);
+    dfree(ctx->d_rod);
+    dfree(ctx->d_obs_col);
+    dfree(ctx->d_od_ptr);
+    dfree(ctx->d_od_routes);
+    dfree(ctx->d_task_od);
+    dfree(ctx->d_pair_k);
+    dfree(ctx->d_pair_j);
+    dfree(ctx->d_pair_o);
+    dfree(ctx->d_rpp);
+    dfree(ctx->d_len);
+    dfree(ctx->d_rpack);
+    dfree(ctx->d_queue);
+    dfree(ctx->d_err);
+    if (ctx->d_rbuf) cudaFree(ctx->d_rbuf);
+    dfree(ctx->d_gring);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+int dode_set_stream(dode_ctx *ctx, void *stream) {
+    if (!ctx) return DODE_ERR_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    ctx->opt.stream = stream;
+    return DODE_OK;
+}
+
+int dode_set_launch(dode_ctx *ctx, int32_t block_threads, int32_t ctas_per_sm) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (block_threads < 0 || block_threads > 1024 || block_threads % 32 || ctas_per_sm < 0 || ctas_per_sm > 8)
+        return fail(ctx, DODE_ERR_ARG, "launch shape: block_threads multiple of 32 up to 1024, ctas_per_sm 0..8");
+    ctx->opt.block_threads = block_threads;
+    ctx->opt.ctas_per_sm = ctas_per_sm;
+    return DODE_OK;
+}
+
+int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const float *speeds, const uint8_t *mask,
+                  int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (n_days < 1 || !counts || !speeds || bad_ptr_kind(ptr_kind)) return fail(ctx, DODE_ERR_ARG, "set_days arguments");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    const int D = n_days, N = ctx->N, Np = ctx->Np, A = ctx->A, O = ctx->O;
+    if (D != ctx->D) {
+        free_days(ctx);
+        CU(dalloc(&ctx->d_ticks, (size_t)D * A * Np));
+        CU(dalloc(&ctx->d_counts, (size_t)D * O * Np));
+        CU(dalloc(&ctx->d_mask, (size_t)D * O * ctx->Nw));
+        CU(dalloc(&ctx->d_colact, (size_t)D * ctx->Ow));
+        CU(dalloc(&ctx->d_C, (size_t)D * ctx->P * Np));
+        CU(dalloc(&ctx->d_pt, (size_t)D * ctx->P * Np));
+        CU(dalloc(&ctx->d_maxoff, (size_t)D));
+        CU(dalloc(&ctx->d_repairs, (size_t)D));
+        CU(dalloc(&ctx->d_tab_off, (size_t)D));
+        CU(dalloc(&ctx->d_q, (size_t)D * ctx->K * Np));
+        CU(dalloc(&ctx->d_G, (size_t)D * ctx->K * Np));
+        CU(dalloc(&ctx->d_qb, (size_t)D * ctx->K * Np));
+        CU(dalloc(&ctx->d_qtmp, (size_t)D * ctx->K * Np));
+        CU(dalloc(&ctx->d_loss, (size_t)D));
+        CU(dalloc(&ctx->d_dtheta, (size_t)D));
+        ctx->D = D;
+    }
+    ctx->plain_ready = false;
+    ctx->trace_iters = -1;
+    // speeds -> ticks (staged through the device when on the host)
+    const size_t sp_bytes = (size_t)D * N * A * sizeof(float);
+    const size_t ct_bytes = (size_t)D * N * O * sizeof(float);
+    const size_t mk_bytes = mask ? (size_t)D * N * O : 0;
+    if (ptr_kind == DODE_PTR_HOST) {
+        rc = stage(ctx, std::max(sp_bytes, ct_bytes + mk_bytes));
+        if (rc) return rc;
+    }
+    const void *dsp = nullptr;
+    rc = input(ctx, speeds, sp_bytes, ptr_kind, 0, &dsp);
+    if (rc) return rc;
+    CU(cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));
+    CUL(launch_ticks(static_cast<const float *>(dsp), ctx->d_len, D, N, Np, A, ctx->tps, ctx->d_ticks, ctx->d_err + 3,
+                     ctx->d_err, ctx->stream));
+    CU(cudaMemcpyAsync(&ctx->max_tick, ctx->d_err + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    rc = check_device_error(ctx);
+    if (rc) {
+        free_days(ctx);
+        return rc;
+    }
+    // trajectories: pass 1 (route times, offsets, repair counts)
+    CU(cudaMemsetAsync(ctx->d_maxoff, 0, (size_t)D * sizeof(int32_t), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_repairs, 0, (size_t)D * sizeof(unsigned long long), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_tab_off, 0xff, (size_t)D * sizeof(int64_t), ctx->stream));
+    PrepParams pp{};
+    pp.N = N;
+    pp.Np = Np;
+    pp.A = A;
+    pp.P = ctx->P;
+    pp.tps = ctx->tps;
+    pp.div = ctx->div;
+    pp.rptr = ctx->d_rptr;
+    pp.rlinks = ctx->d_rlinks;
+    pp.ticks = ctx->d_ticks;
+    pp.C = ctx->d_C;
+    pp.maxoff = ctx->d_maxoff;
+    pp.repairs = ctx->d_repairs;
+    pp.tab_off = ctx->d_tab_off;
+    pp.traj_tab = nullptr;
+    pp.n_days = D;
+    CUL(launch_prepare(pp, ctx->stream));
+    ctx->h_maxoff.resize(D);
+    ctx->h_repairs.resize(D);
+    CU(cudaMemcpyAsync(ctx->h_maxoff.data(), ctx->d_maxoff, D * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->h_repairs.data(), ctx->d_repairs, D * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->maxoff_max = *std::max_element(ctx->h_maxoff.begin(), ctx->h_maxoff.end());
+    // pass 2 for days that needed FIFO repairs: keep their exact trajectories
+    std::vector<int64_t> off(D, -1);
+    const size_t per_day = (size_t)(ctx->L + ctx->P) * (N + 1);
+    size_t n_tab = 0;
+    for (int d = 0; d < D; ++d)
+        if (ctx->h_repairs[d] > 0) {
+            off[d] = (int64_t)(n_tab * per_day);
+            ++n_tab;
+        }
+    dfree(ctx->d_traj_tab);
+    if (n_tab > 0) {
+        CU(dalloc(&ctx->d_traj_tab, n_tab * per_day));
+        CU(cudaMemcpyAsync(ctx->d_tab_off, off.data(), D * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemsetAsync(ctx->d_repairs, 0, (size_t)D * sizeof(unsigned long long), ctx->stream));
+        pp.traj_tab = ctx->d_traj_tab;
+        CUL(launch_prepare(pp, ctx->stream));
+    }
+    // counts / mask
+    rc = dode_set_counts(ctx, counts, mask, ptr_kind);
+    if (rc) return rc;
+    // fresh solver state
+    CU(cudaMemsetAsync(ctx->d_q, 0, (size_t)D * ctx->K * Np * sizeof(float), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_G, 0, (size_t)D * ctx->K * Np * sizeof(float), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_set_counts(dode_ctx *ctx, const float *counts, const uint8_t *mask, int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!counts || bad_ptr_kind(ptr_kind)) return fail(ctx, DODE_ERR_ARG, "set_counts arguments");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    const int D = ctx->D, N = ctx->N, O = ctx->O;
+    const size_t ct_bytes = (size_t)D * N * O * sizeof(float);
+    const size_t mk_bytes = (size_t)D * N * O;
+    if (ptr_kind == DODE_PTR_HOST) {
+        rc = stage(ctx, ct_bytes + mk_bytes);
+        if (rc) return rc;
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    const void *dct = nullptr;
+    rc = input(ctx, counts, ct_bytes, ptr_kind, 0, &dct);
+    if (rc) return rc;
+    CUL(launch_transpose_in(static_cast<const float *>(dct), ctx->d_counts, D, N, ctx->Np, O, ctx->stream));
+    const void *dmk = nullptr;
+    if (mask) {
+        rc = input(ctx, mask, mk_bytes, ptr_kind, ct_bytes, &dmk);
+        if (rc) return rc;
+    }
+    CUL(launch_pack_mask(static_cast<const uint8_t *>(dmk), ctx->d_mask, ctx->d_colact, D, N, ctx->Nw, O, ctx->Ow,
+                        ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_get_state(dode_ctx *ctx, float *q, float *G, int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (bad_ptr_kind(ptr_kind)) return fail(ctx, DODE_ERR_ARG, "ptr_kind");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    if (q && (rc = output_odmajor(ctx, ctx->d_q, q, ctx->K, 1.f, ptr_kind))) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (G && (rc = output_odmajor(ctx, ctx->d_G, G, ctx->K, 1.f, ptr_kind))) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_set_state(dode_ctx *ctx, const float *q, const float *G, int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (bad_ptr_kind(ptr_kind)) return fail(ctx, DODE_ERR_ARG, "ptr_kind");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (q && (rc = input_odmajor(ctx, q, ctx->d_q, ctx->K, ptr_kind))) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (G && (rc = input_odmajor(ctx, G, ctx->d_G, ctx->K, ptr_kind))) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q_out, double *loss_out,
+               int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (iters < 0 || !(step > 0.f) || !std::isfinite(step) || batch < 0 || bad_ptr_kind(ptr_kind))
+        return fail(ctx, DODE_ERR_ARG, "solve arguments");
+    if (ctx->opt.row_chunk > 0) return fail(ctx, DODE_ERR_UNSUPPORTED, "row_chunk > 0 is not supported by this build");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    const int D = ctx->D;
+    if (ctx->opt.form == DODE_FORM_PLAIN) {
+        PlainParams pp;
+        rc = plain_prepare(ctx, ctx->opt.theta_per_min, &pp);
+        if (rc) return rc;
+        if (!ctx->d_xout) CU(dalloc(&ctx->d_xout, (size_t)D * ctx->O * ctx->Np));
+        const size_t need = (size_t)(iters + 1) * D;
+        if (need > ctx->ptrace_cap) {
+            CU(dalloc(&ctx->d_ptrace, need));
+            ctx->ptrace_cap = need;
+        }
+        CU(cudaMemsetAsync(ctx->d_ptrace, 0, need * sizeof(double), ctx->stream));
+        const size_t xbytes = (size_t)D * ctx->O * ctx->Np * sizeof(float);
+        CU(cudaEventRecord(ctx->ev0, ctx->stream));
+        for (int it = 0; it <= iters; ++it) {
+            CU(cudaMemsetAsync(ctx->d_xout, 0, xbytes, ctx->stream));
+            CUL(launch_plain_forward(pp, ctx->d_q, ctx->d_xout, ctx->stream));
+            CUL(launch_plain_residual(pp, ctx->d_counts, ctx->d_mask, ctx->d_xout, ctx->d_ptrace + (size_t)it * D,
+                                     nullptr, ctx->stream));
+            if (it < iters)
+                CUL(launch_plain_adjoint_step(pp, ctx->d_xout, ctx->d_q, ctx->d_G, step, ctx->opt.eps, ctx->stream));
+        }
+        CU(cudaEventRecord(ctx->ev1, ctx->stream));
+        ctx->last_launches = 1 + 3LL * iters + 2;
+        CU(cudaMemcpyAsync(ctx->d_loss, ctx->d_ptrace + (size_t)iters * D, D * sizeof(double),
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+    } else {
+        if ((size_t)iters * D > ctx->trace_cap) {
+            CU(dalloc(&ctx->d_trace, (size_t)iters * D));
+            ctx->trace_cap = (size_t)iters * D;
+        }
+        FusedParams p = base_params(ctx);
+        p.mode = MODE_SOLVE;
+        p.iters = iters;
+        p.eta = step;
+        p.trace = iters > 0 ? ctx->d_trace : nullptr;
+        if (ctx->opt.precision == DODE_PREC_BF16)
+            CUL(launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, ctx->stream));
+        rc = run_fused(ctx, p, ctx->opt.precision);
+        if (rc) return rc;
+    }
+    ctx->trace_iters = iters;
+    rc = finish_timing(ctx);
+    if (rc) return rc;
+    rc = check_device_error(ctx);
+    if (rc) return rc;
+    if (q_out && (rc = output_odmajor(ctx, ctx->d_q, q_out, ctx->K, 1.f, ptr_kind))) return rc;
+    if (loss_out && (rc = output_plain(ctx, ctx->d_loss, loss_out, D * sizeof(double), ptr_kind))) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_get_loss_trace(dode_ctx *ctx, float *trace, int32_t iters) {
+    if (!ctx || !trace) return DODE_ERR_ARG;
+    if (ctx->trace_iters < 0) return fail(ctx, DODE_ERR_STATE, "no solve since the days were loaded");
+    if (iters != ctx->trace_iters) return fail(ctx, DODE_ERR_ARG, "iters differs from the last solve");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    const size_t n = (size_t)iters * ctx->D;
+    if (n == 0) return DODE_OK;
+    if (ctx->opt.form == DODE_FORM_PLAIN) {
+        std::vector<double> tmp(n);
+        CU(cudaMemcpyAsync(tmp.data(), ctx->d_ptrace, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        for (size_t i = 0; i < n; ++i) trace[i] = (float)tmp[i];
+    } else {
+        CU(cudaMemcpyAsync(trace, ctx->d_trace, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return DODE_OK;
+}
+
+static int fused_eval(dode_ctx *ctx, int mode, const float *q, float theta, int ptr_kind) {
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    rc = input_odmajor(ctx, q, ctx->d_qtmp, ctx->K, ptr_kind);
+    if (rc) return rc;
+    FusedParams p = base_params(ctx);
+    p.mode = mode;
+    p.theta = theta;
+    p.q = ctx->d_qtmp;
+    p.G = nullptr;
+    if (ctx->opt.precision == DODE_PREC_BF16)
+        CUL(launch_to_bf16(ctx->d_qtmp, ctx->d_qb, (size_t)ctx->D * ctx->K * ctx->Np, ctx->stream));
+    if (mode == MODE_FORWARD) {
+        if (!ctx->d_xout) CU(dalloc(&ctx->d_xout, (size_t)ctx->D * ctx->O * ctx->Np));
+        p.xout = ctx->d_xout;
+    }
+    if (mode == MODE_LOSS_GRAD) {
+        if (!ctx->d_gout) CU(dalloc(&ctx->d_gout, (size_t)ctx->D * ctx->K * ctx->Np));
+        p.gout = ctx->d_gout;
+    }
+    rc = run_fused(ctx, p, ctx->opt.precision);
+    if (rc) return rc;
+    rc = finish_timing(ctx);
+    if (rc) return rc;
+    return check_device_error(ctx);
+}
+
+int dode_forward(dode_ctx *ctx, const float *q, float *xhat, int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!q || !xhat || bad_ptr_kind(ptr_kind)) return fail(ctx, DODE_ERR_ARG, "forward arguments");
+    int rc = fused_eval(ctx, MODE_FORWARD, q, ctx->opt.theta_per_min, ptr_kind);
+    if (rc) return rc;
+    rc = output_odmajor(ctx, ctx->d_xout, xhat, ctx->O, 1.f, ptr_kind);
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!q || !loss || bad_ptr_kind(ptr_kind) || !std::isfinite(theta)) return fail(ctx, DODE_ERR_ARG, "loss arguments");
+    int rc = fused_eval(ctx, MODE_LOSS, q, theta, ptr_kind);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(loss, ctx->d_loss, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, float *dq, double *dtheta,
+                   int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!q || !loss || bad_ptr_kind(ptr_kind) || !std::isfinite(theta))
+        return fail(ctx, DODE_ERR_ARG, "loss_grad arguments");
+    int rc = fused_eval(ctx, MODE_LOSS_GRAD, q, theta, ptr_kind);
+    if (rc) return rc;
+    if (dq && (rc = output_odmajor(ctx, ctx->d_gout, dq, ctx->K, 1.f, ptr_kind))) return rc;
+    CU(cudaMemcpyAsync(loss, ctx->d_loss, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (dtheta) CU(cudaMemcpyAsync(dtheta, ctx->d_dtheta, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_get_ticks(dode_ctx *ctx, int32_t day, int32_t *out) {
+    if (!ctx || !out) return DODE_ERR_ARG;
+    if (day < 0 || day >= ctx->D) return fail(ctx, DODE_ERR_ARG, "day out of range");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    std::vector<int32_t> t((size_t)ctx->A * ctx->Np);
+    CU(cudaMemcpyAsync(t.data(), ctx->d_ticks + (size_t)day * ctx->A * ctx->Np, t.size() * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int h = 0; h < ctx->N; ++h)
+        for (int a = 0; a < ctx->A; ++a) out[(size_t)h * ctx->A + a] = t[(size_t)a * ctx->Np + h];
+    return DODE_OK;
+}
+
+int dode_get_route_times(dode_ctx *ctx, int32_t day, float *out) {
+    if (!ctx || !out) return DODE_ERR_ARG;
+    if (day < 0 || day >= ctx->D) return fail(ctx, DODE_ERR_ARG, "day out of range");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    std::vector<float> t((size_t)ctx->P * ctx->Np);
+    CU(cudaMemcpyAsync(t.data(), ctx->d_C + (size_t)day * ctx->P * ctx->Np, t.size() * sizeof(float),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int h = 0; h < ctx->N; ++h)
+        for (int k = 0; k < ctx->P; ++k) out[(size_t)h * ctx->P + k] = t[(size_t)k * ctx->Np + h];
+    return DODE_OK;
+}
+
+int dode_get_day_info(dode_ctx *ctx, int32_t day, int64_t *n_repairs, int32_t *max_offset) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (day < 0 || day >= ctx->D) return fail(ctx, DODE_ERR_ARG, "day out of range");
+    if (n_repairs) *n_repairs = (int64_t)ctx->h_repairs[day];
+    if (max_offset) *max_offset = ctx->h_maxoff[day];
+    return DODE_OK;
+}
+
+int dode_get_dar(dode_ctx *ctx, int32_t day, int64_t *n, int32_t *kjh, float *rho) {
+    if (!ctx || !n) return DODE_ERR_ARG;
+    if (day < 0 || day >= ctx->D) return fail(ctx, DODE_ERR_ARG, "day out of range");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    // every (route, position) pair, not only observed links
+    std::vector<int32_t> pk, pj, po, rpp(ctx->P + 1, 0);
+    for (int k = 0; k < ctx->P; ++k) {
+        for (int j = ctx->rptr[k]; j < ctx->rptr[k + 1]; ++j) {
+            pk.push_back(k);
+            pj.push_back(j - ctx->rptr[k]);
+            po.push_back(0);
+        }
+        rpp[k + 1] = (int32_t)pk.size();
+    }
+    int32_t *d_pk = nullptr, *d_pj = nullptr, *d_po = nullptr, *d_rpp = nullptr;
+    int4 *d_rec = nullptr;
+    const int npairs = (int)pk.size();
+    CU(upload(&d_pk, pk, ctx->stream));
+    CU(upload(&d_pj, pj, ctx->stream));
+    CU(upload(&d_po, po, ctx->stream));
+    CU(upload(&d_rpp, rpp, ctx->stream));
+    CU(dalloc(&d_rec, (size_t)npairs * ctx->N));
+    PlainParams p{};
+    p.N = ctx->N;
+    p.Np = ctx->Np;
+    p.A = ctx->A;
+    p.P = ctx->P;
+    p.n_pairs = npairs;
+    p.div = ctx->div;
+    p.rptr = ctx->d_rptr;
+    p.rlinks = ctx->d_rlinks;
+    p.pair_k = d_pk;
+    p.pair_j = d_pj;
+    p.pair_o = d_po;
+    p.route_pair_ptr = d_rpp;
+    p.ticks = ctx->d_ticks + (size_t)day * ctx->A * ctx->Np;
+    p.tab_off = ctx->d_tab_off + day;
+    p.traj_tab = ctx->d_traj_tab;
+    p.rec = d_rec;
+    p.n_days = 1;
+    p.err = ctx->d_err;
+    CUL(launch_plain_build(p, ctx->stream));
+    std::vector<int4> rec((size_t)npairs * ctx->N);
+    CU(cudaMemcpyAsync(rec.data(), d_rec, rec.size() * sizeof(int4), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaFree(d_pk);
+    cudaFree(d_pj);
+    cudaFree(d_po);
+    cudaFree(d_rpp);
+    cudaFree(d_rec);
+    rc = check_device_error(ctx);
+    if (rc) return rc;
+    int64_t m = 0;
+    for (int pi = 0; pi < npairs; ++pi) {
+        for (int b = 0; b < ctx->N; ++b) {
+            const int4 r = rec[(size_t)pi * ctx->N + b];
+            const int cnt = r.x >> 16, h2 = r.x & 0xffff;
+            const int vals[3] = {r.y, r.z, r.w};
+            for (int c = 0; c < cnt; ++c) {
+                if (kjh) {
+                    kjh[4 * m + 0] = pk[pi];
+                    kjh[4 * m + 1] = pj[pi];
+                    kjh[4 * m + 2] = b;
+                    kjh[4 * m + 3] = h2 + c;
+                }
+                if (rho) {
+                    float f;
+                    std::memcpy(&f, &vals[c], sizeof f);
+                    rho[m] = f;
+                }
+                ++m;
+            }
+        }
+    }
+    *n = m;
+    return DODE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// dode_internal.cuh -- device-side layouts, parameter blocks and helpers of libdode.
+//
+// Internal layouts put TIME innermost so that the 32 lanes of a warp, which
+// walk 32 consecutive departure boundaries of one route, touch consecutive
+// words:
+//   ticks   int32 [D][A][Np]     link travel time (ticks) by entry interval
+//   counts  f32   [D][O][Np]     observed link counts
+//   mask    u32   [D][O][Nw]     bit h of word h/32: cell (h, o) observed
+//   colact  u32   [D][Ow]        bit o: link column o has any observation that day
+//   C       f32   [D][P][Np]     route time (minutes) of departure interval h
+//   q, G    f32   [D][K][Np]     OD flows and Adagrad accumulator
+//   r slot  f32/bf16 [O][Np]     residual of one resident day (per CTA)
+// with Np = N + 1 rounded up to a multiple of 32 and Nw = ceil(N / 32).  The
+// ABI's time-major layouts (Table "DODE framework variable vectorization") are
+// converted on entry and exit by tiled transposes.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dode {
+
+constexpr int kWarp = 32;
+constexpr int kTileW = 31;            // windows per warp task (32 boundaries)
+constexpr int kMaxRouteLinks = 64;
+
+enum Mode : int { MODE_SOLVE = 0, MODE_FORWARD = 1, MODE_LOSS = 2, MODE_LOSS_GRAD = 3 };
+
+// floor(t / ipt) for 0 <= t < 2^31 via a 32-bit magic multiplier:
+// with l = ceil(log2 ipt) and M = ceil(2^(31+l) / ipt) < 2^32,
+// floor(t / ipt) = umulhi(t, M) >> (l - 1) for every t < 2^31.
+struct IntervalDiv {
+    uint32_t magic;
+    int shift;
+    int ipt;
+};
+
+// Requires ipt >= 2 (validated when the context is created).
+__host__ __device__ inline IntervalDiv make_interval_div(int ipt) {
+    IntervalDiv d;
+    int l = 0;
+    while ((1u << l) < (uint32_t)ipt) ++l;
+    d.ipt = ipt;
+    uint64_t num = 1ull << (31 + l);
+    d.magic = (uint32_t)((num + (uint64_t)ipt - 1) / (uint64_t)ipt);
+    d.shift = l - 1;
+    return d;
+}
+
+__device__ __forceinline__ int interval_of(int t, const IntervalDiv &d) {
+    return (int)(__umulhi((uint32_t)t, d.magic) >> d.shift);
+}
+
+struct FusedParams {
+    // sizes
+    int N, Np, Nw, A, O, Ow, K, P;
+    IntervalDiv div;
+    // network / routes (device)
+    const int32_t *rptr;       // [P+1]
+    const int32_t *rlinks;     // [L]
+    const int32_t *obs_col;    // [A]
+    const int32_t *od_ptr;     // [K+1]
+    const int32_t *od_routes;  // [P] routes grouped by OD
+    const int32_t *task_od;    // [K] OD processing order (largest work first)
+    const int2 *rpack;         // [L] (link, observed column or -1) of every route position
+    const float *pt;           // [D][P][Np] route choice for the call's theta
+    // per-day inputs
+    const int32_t *ticks;
+    const float *counts;
+    const uint32_t *mask;
+    const uint32_t *colact;
+    const float *C;
+    const int32_t *maxoff;     // [D]
+    const int64_t *tab_off;    // [D] offset of the repaired trajectory table, -1 if none
+    const int32_t *traj_tab;
+    // state / operands
+    float *q;                  // [D][K][Np] FP32 (master in SOLVE, input otherwise)
+    float *G;
+    __nv_bfloat16 *qb;         // [D][K][Np] BF16 operand copy (BF16 form)
+    void *rbuf;                // [grid][O][Np] residual slots (f32 or bf16)
+    float *gring;              // [grid][O][Np] accumulators when the ring lives in global memory
+    // outputs
+    double *loss;              // [D]
+    float *trace;              // [iters][D] or null
+    double *dtheta;            // [D] (LOSS_GRAD)
+    float *gout;               // [D][K][Np] 2 B^T r (LOSS_GRAD)
+    float *xout;               // [D][O][Np] (FORWARD)
+    // control
+    int n_days, iters, mode;
+    float eta, eps, theta;
+    int ring_rows;             // R rows per observed link in the shared ring, 0 = global ring
+    int tick_rows;             // RW tick rows per link staged in shared memory, 0 = read global
+    int tiles_per_phase;       // F (upper bound; the kernel lowers it for days with long trips)
+    int *queue;
+    int *err;
+};
+
+struct PrepParams {
+    int N, Np, A, P, tps;
+    IntervalDiv div;
+    const int32_t *rptr, *rlinks;
+    const int32_t *ticks;      // [D][A][Np]
+    float *C;                  // [D][P][Np]
+    int32_t *maxoff;           // [D]
+    unsigned long long *repairs;  // [D]
+    const int64_t *tab_off;    // [D] or null (pass 1)
+    int32_t *traj_tab;
+    int n_days;
+};
+
+struct PlainParams {
+    int N, Np, Nw, A, O, K, P, n_pairs;
+    IntervalDiv div;
+    const int32_t *rptr, *rlinks, *rod, *od_ptr, *od_routes;
+    const int32_t *pair_k, *pair_j, *pair_o;   // [n_pairs] (route, link position, observed column)
+    const int32_t *route_pair_ptr;             // [P+1] pairs of route k
+    const int32_t *ticks;
+    const int64_t *tab_off;
+    const int32_t *traj_tab;
+    const float *C;
+    float theta;
+    int4 *rec;                 // [D][n_pairs][N] DAR records
+    float *p;                  // [D][P][Np] route choice
+    int n_days;
+    int *err;
+};
+
+// error codes mirrored from dode.h for device use
+constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrUnsupported = -10;
+
+__device__ __forceinline__ void set_error(int *err, int code, long long index) {
+    if (atomicCAS(err, 0, code) == 0) {
+        err[1] = (int)(index & 0x7fffffff);
+        err[2] = (int)(index >> 31);
+    }
+}
+
+// launchers (defined in the .cu files)
+cudaError_t launch_ticks(const float *speeds, const float *len, int D, int N, int Np, int A, int tps,
+                         int32_t *ticks, int *maxtick, int *err, cudaStream_t s);
+cudaError_t launch_prepare(const PrepParams &p, cudaStream_t s);
+cudaError_t launch_transpose_in(const float *src, float *dst, int D, int N, int Np, int M,
+                                cudaStream_t s);  // [D][N][M] -> [D][M][Np]
+cudaError_t launch_transpose_out(const float *src, float *dst, int D, int N, int Np, int M, float scale,
+                                 cudaStream_t s); // [D][M][Np] -> [D][N][M]
+cudaError_t launch_pack_mask(const uint8_t *mask, uint32_t *bits, uint32_t *colact, int D, int N, int Nw,
+                             int O, int Ow, cudaStream_t s);
+cudaError_t launch_to_bf16(const float *src, __nv_bfloat16 *dst, size_t n, cudaStream_t s);
+cudaError_t launch_route_choice(const float *C, const int32_t *rod, const int32_t *od_ptr, const int32_t *od_routes,
+                                float theta, int D, int P, int N, int Np, float *pt, cudaStream_t s);
+cudaError_t launch_fused(const FusedParams &p, int precision, int grid, int block, size_t smem,
+                         cudaStream_t s);
+cudaError_t fused_occupancy(int precision, int block, size_t smem, int *blocks_per_sm);
+cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
+cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
+cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);
+cudaError_t launch_plain_residual(const PlainParams &p, const float *counts, const uint32_t *mask,
+                                  float *xr, double *loss, float *trace_row, cudaStream_t s);
+cudaError_t launch_plain_adjoint_step(const PlainParams &p, const float *r, float *q, float *G, float eta,
+                                      float eps, cudaStream_t s);
+
+}  // namespace dode

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads and
+exports every entry point declared in include/dode.h, and argument validation
+in dode_create rejects bad networks before any device call."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1901_09266_gb300 import build, dode, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return dode.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "dode.h")).read()
+    declared = set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(dode_\w+)\s*\(", hdr, re.M))
+    assert len(declared) >= 20
+    assert declared == set(dode.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_default_options(lib):
+    o = dode.default_options()
+    assert (o.n_intervals, o.interval_s, o.ticks_per_s) == (288, 300, 16)
+    assert o.theta_per_min == pytest.approx(0.1)
+    assert o.eps == pytest.approx(1e-10)
+    assert o.form == dode.FORM_FUSED and o.precision == dode.PREC_FP32
+
+
+def _ctx_args(w):
+    r = w.routes
+    return dict(n_nodes=w.net.n_nodes, link_tail=w.net.link_tail, link_head=w.net.link_head,
+                link_len_mi=w.net.link_len_mi, obs_links=w.net.obs_links, n_od=r.n_od, route_od=r.route_od,
+                route_ptr=r.route_ptr, route_links=r.route_links)
+
+
+def test_validation_rejects_bad_networks(lib):
+    w = synth.corridor_7day()
+    base = _ctx_args(w)
+
+    def expect(code, **override):
+        args = dict(base)
+        args.update(override)
+        with pytest.raises(dode.DodeError) as e:
+            dode.Context(**args)
+        assert e.value.code == code
+
+    links = w.routes.route_links.copy()
+    # swap two links of route 0 -> not contiguous
+    links[[0, 1]] = links[[1, 0]]
+    expect(dode.ERR_ROUTE_NOT_CONTIGUOUS, route_links=links)
+    # a route that revisits a link: a -> b -> a is impossible without a cycle; build one
+    tail = np.array([0, 1], np.int32)
+    head = np.array([1, 0], np.int32)
+    with pytest.raises(dode.DodeError) as e:
+        dode.Context(2, tail, head, np.ones(2, np.float32), np.array([0], np.int32), 1, np.array([0], np.int32),
+                     np.array([0, 3], np.int32), np.array([0, 1, 0], np.int32))
+    assert e.value.code == dode.ERR_ROUTE_REPEATS_LINK
+    expect(dode.ERR_ARG, obs_links=np.array([0, 0], np.int32))               # duplicated observed link
+    expect(dode.ERR_ARG, obs_links=np.array([10 ** 6], np.int32))            # out of range
+    bad_len = w.net.link_len_mi.copy()
+    bad_len[3] = 0.0
+    expect(dode.ERR_ARG, link_len_mi=bad_len)
+    bad_od = w.routes.route_od.copy()
+    bad_od[:] = 0                                                           # ODs 1.. have no route
+    expect(dode.ERR_ARG, route_od=bad_od)
+    long_ptr = w.routes.route_ptr.copy()
+    long_ptr[1] = 0                                                         # empty route
+    expect(dode.ERR_ARG, route_ptr=long_ptr)
+
+
+def test_interval_magic_division_is_exact():
+    """floor(t / ipt) by the 32-bit multiply-high used in the kernels, checked
+    against integer division for every interval length up to 2^16 ticks on the
+    boundary values and random t < 2^31 (the same arithmetic, in numpy uint64)."""
+    rng = np.random.default_rng(0)
+    for ipt in list(range(1, 300)) + [960, 4800, 9600, 57600, 65536, 65535, 86400 * 16 // 288]:
+        ll = 0
+        while (1 << ll) < ipt:
+            ll += 1
+        if ipt == 1:
+            continue
+        magic = ((1 << (31 + ll)) + ipt - 1) // ipt
+        assert magic < (1 << 32)
+        t = np.concatenate([rng.integers(0, 2 ** 31, 20000), np.arange(0, 2 ** 31 - ipt, 2 ** 31 // 997)])
+        t = np.concatenate([t, (t // ipt) * ipt - 1, (t // ipt) * ipt, (t // ipt) * ipt + ipt - 1]).clip(0, 2 ** 31 - 1)
+        t = t.astype(np.uint64)
+        got = ((t * np.uint64(magic)) >> np.uint64(32)) >> np.uint64(ll - 1)
+        np.testing.assert_array_equal(got, t // np.uint64(ipt))

@@ -1,0 +1,47 @@
+"""The multi-rank host logic of bench.py on CPU ranks (gloo, world size 2):
+day sharding gives every rank its own disjoint days (weak scaling) and the
+step time is the maximum over ranks.  No GPU is involved."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port() -> int:
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    dist = bench.dist_init("gloo")
+    days = bench.shard_days(10, rank, world)
+    t = bench.dist_max(1.5 + rank)
+    bench.dist_barrier()
+    out[rank] = (days, t)
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharding_and_max_time():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    mgr = mp.Manager()
+    out = mgr.dict()
+    port = _free_port()
+    mp.start_processes(_worker, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
+    d0, t0 = out[0]
+    d1, t1 = out[1]
+    assert d0 == list(range(0, 10)) and d1 == list(range(10, 20))
+    assert set(d0).isdisjoint(d1)
+    assert t0 == t1 == 2.5
+
+
+def test_algorithmic_bytes_of_the_3yr_corridor():
+    import bench
+    # counts 4*288*400 + mask 288*400/8 + ticks 2*288*438 + q 8*288*150 + G 8*288*150 + 8
+    assert bench.algorithmic_bytes(288, 400, 438, 150) == 460800 + 14400 + 252288 + 345600 + 345600 + 8
