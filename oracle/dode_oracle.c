@@ -452,7 +452,7 @@ double or_solve_day(const or_day *d, const float *counts, const uint8_t *mask, i
 /* dp_k/dtheta = p_k (-C_k + sum_{k' in od} p_k' C_k').                      */
 /* ------------------------------------------------------------------------ */
 double or_loss_grad_day(const or_day *d, const float *counts, const uint8_t *mask, const double *q,
-                        double *dq, double *dtheta) {
+                        double *dq, double *dtheta, double *dtheta_abs) {
     const or_net *n = d->net;
     size_t rows = (size_t)n->N * n->O, cols = (size_t)n->N * n->K;
     double *xhat = (double *)malloc(sizeof(double) * rows);
@@ -472,7 +472,7 @@ double or_loss_grad_day(const or_day *d, const float *counts, const uint8_t *mas
             if (o < 0) continue;
             gp[(size_t)x->h1 * n->P + x->k] += x->rho * r[(size_t)x->h2 * n->O + o];
         }
-        double acc = 0.0;
+        double acc = 0.0, acc_abs = 0.0;
         for (int32_t h = 0; h < n->N; ++h) {
             for (int32_t k = 0; k < n->P; ++k) {
                 int32_t od = n->rod[k];
@@ -481,10 +481,15 @@ double or_loss_grad_day(const or_day *d, const float *counts, const uint8_t *mas
                     if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->C[(size_t)h * n->P + k2];
                 double pk = d->p[(size_t)h * n->P + k];
                 double dp = pk * (-d->C[(size_t)h * n->P + k] + mean_c);
-                acc += 2.0 * q[(size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * dp;
+                const double term = 2.0 * q[(size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * dp;
+                acc += term;
+                acc_abs += fabs(term);
             }
         }
         *dtheta = acc;
+        /* sum of |terms|: the scale against which a rounding error of the
+           cancelling sum is measured */
+        if (dtheta_abs) *dtheta_abs = acc_abs;
         free(gp);
     }
     free(xhat); free(r);

@@ -57,7 +57,7 @@ def lib():
         L.or_solve_day.argtypes = [ct.c_void_p, _f32p, _u8p, ct.c_int32, ct.c_double, ct.c_double,
                                    ct.c_int32, ct.c_uint64, ct.c_int32, _f64p, _f64p, _f64p]
         L.or_loss_grad_day.restype = ct.c_double
-        L.or_loss_grad_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p, _f64p, _f64p]
+        L.or_loss_grad_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p, _f64p, _f64p, _f64p]
         L.or_splitmix64_next.restype = ct.c_uint64
         L.or_splitmix64_next.argtypes = [ct.POINTER(ct.c_uint64)]
         L.or_permute_rows.argtypes = [_i32p, ct.c_int32, ct.c_uint64, ct.c_int32, ct.c_int32]
@@ -246,14 +246,17 @@ class Day:
                                   None if tr is None else _p(tr, _f64p))
         return (q, G, loss, tr[:iters]) if trace else (q, G, loss)
 
-    def loss_grad(self, counts, mask, q):
+    def loss_grad(self, counts, mask, q, with_scale=False):
+        """(loss, dL/dq, dL/dtheta) -- and, with ``with_scale``, the sum of the
+        absolute values of the dL/dtheta terms (the scale of its rounding error)."""
         n = self.net
         cc, mm, qq = _c(counts, np.float32), _c(mask, np.uint8), _c(q, np.float64)
         dq = np.zeros((n.N, n.K))
         dth = ct.c_double(0.0)
+        dabs = ct.c_double(0.0)
         loss = lib().or_loss_grad_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p), _p(dq, _f64p),
-                                      ct.byref(dth))
-        return loss, dq, dth.value
+                                      ct.byref(dth), ct.byref(dabs))
+        return (loss, dq, dth.value, dabs.value) if with_scale else (loss, dq, dth.value)
 
 
 def splitmix64(seed: int, n: int) -> list:

@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/dode.h"
+#include "dode.h"
 #include "dode_internal.cuh"
 
 using namespace dode;
@@ -214,11 +214,22 @@ struct FusedShape {
 };
 
 // Launch shape of the fused kernel: CTA size, CTAs per SM and the shared-memory
-// windows.  A phase of F tiles needs R = 31 F + maxoff + 2 ring rows per
-// observed link (FP32) and RW = 31 F + maxoff + 1 tick rows per link (uint16,
-// only when every tick fits 16 bits).  The largest F up to 3 that fits is
-// taken; otherwise ticks are read from global memory, and if even the ring
-// does not fit the link flows accumulate in global memory.
+// windows.  The dynamic shared memory holds the OD / route tables, the day's
+// active-column bits, the accumulators (R = 31 F + maxoff + 2 rows per observed
+// link, 32-bit words) and, when every tick fits 16 bits, the tick window
+// (RW = 31 F + maxoff + 1 rows per link).  The largest F up to 3 that fits is
+// taken; otherwise ticks are read from global memory, and if even the
+// accumulators do not fit the link flows accumulate in global memory.
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+size_t fused_smem_bytes(const dode_ctx *ctx, int R, int RW) {
+    size_t off = align16((size_t)ctx->P * 16) + align16((size_t)ctx->K * 8) + align16((size_t)ctx->K * 4) +
+                 align16((size_t)ctx->Ow * 4);
+    if (R > 0) off = align16(off + (size_t)ctx->O * R * 4);
+    if (RW > 0) off += (size_t)ctx->A * RW * 2;
+    return off;
+}
+
 int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
     const int ntiles = (ctx->N + kTileW - 1) / kTileW;
     const int per_sm = ctx->opt.ctas_per_sm > 0 ? ctx->opt.ctas_per_sm : 1;
@@ -227,28 +238,28 @@ int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
     const size_t reserve = 2048;
     size_t budget = std::min<size_t>(ctx->smem_optin, (size_t)(228 * 1024) / per_sm - 1024);
     budget = budget > reserve ? budget - reserve : 0;
-    const size_t colact = ((size_t)ctx->Ow * sizeof(uint32_t) + 15) & ~(size_t)15;
     const bool ticks16 = ctx->max_tick <= 65535;
     const int mo = ctx->maxoff_max;
     int R = 0, RW = 0, F = 0;
     for (int f = std::min(3, ntiles); f >= 1 && F == 0; --f) {
-        const size_t ring = (size_t)ctx->O * (kTileW * f + mo + 2) * sizeof(float);
-        const size_t tw = ticks16 ? (size_t)ctx->A * (kTileW * f + mo + 1) * sizeof(uint16_t) : (size_t)-1;
-        if (ticks16 && ring + colact + tw <= budget) {
+        const int r = kTileW * f + mo + 2, rw = kTileW * f + mo + 1;
+        if (ticks16 && fused_smem_bytes(ctx, r, rw) <= budget) {
             F = f;
-            R = kTileW * f + mo + 2;
-            RW = kTileW * f + mo + 1;
+            R = r;
+            RW = rw;
         }
     }
     for (int f = std::min(3, ntiles); f >= 1 && F == 0; --f) {
-        const size_t ring = (size_t)ctx->O * (kTileW * f + mo + 2) * sizeof(float);
-        if (ring + colact <= budget) {
+        const int r = kTileW * f + mo + 2;
+        if (fused_smem_bytes(ctx, r, 0) <= budget) {
             F = f;
-            R = kTileW * f + mo + 2;
+            R = r;
         }
     }
     if (F == 0) F = ntiles;
-    const size_t smem = (R ? (size_t)ctx->O * R * sizeof(float) : 0) + colact + (RW ? (size_t)ctx->A * RW * 2 : 0);
+    const size_t smem = fused_smem_bytes(ctx, R, RW);
+    if (smem > budget + reserve)
+        return fail(ctx, DODE_ERR_UNSUPPORTED, "route tables of this network do not fit in shared memory");
     int occ = 0;
     cudaError_t e = fused_occupancy(precision, block, smem, &occ);
     if (e != cudaSuccess) return fail(ctx, DODE_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(e));
@@ -273,11 +284,13 @@ int ensure_slots(dode_ctx *ctx, const FusedShape &s, int precision) {
         CU(cudaMalloc(&ctx->d_rbuf, rb));
         ctx->rbuf_bytes = rb;
     }
-    if (s.ring_rows == 0 && elems * 4 > ctx->gring_bytes) {
+    // global accumulators (no shared ring) or the accumulators' high words
+    const size_t gelems = (size_t)s.grid * ctx->O * std::max(ctx->Np, s.ring_rows);
+    if (gelems * 4 > ctx->gring_bytes) {
         dfree(ctx->d_gring);
         ctx->gring_bytes = 0;
-        CU(cudaMalloc(&ctx->d_gring, elems * 4));
-        ctx->gring_bytes = elems * 4;
+        CU(cudaMalloc(&ctx->d_gring, gelems * 4));
+        ctx->gring_bytes = gelems * 4;
     }
     return DODE_OK;
 }

@@ -14,18 +14,21 @@
 //    tick table (Sec. 2.4, Eq. (cost)).  The route's links are held in registers
 //    as precomputed shared-memory offsets and broadcast by shuffles, so a link
 //    step touches memory only for the tick lookup and the window's one or two
-//    link-interval cells.
+//    link-interval cells.  The OD / route tables sit in shared memory.
 //  * Both sweeps run in phases of F tiles in time order.  A phase stages the
 //    tick rows its trajectories can reach (departure rows plus the day's
 //    largest trip offset, padded past the end of the day with the last row)
 //    from global memory into shared memory.
 //  * Forward sweep (xhat = B q, Eq. (reverse) with (flow)): windows deposit
-//    p q rho into shared-memory accumulators for the phase's arrival rows.
-//    After a phase every interval before the next phase's first departure is
-//    final (no vehicle arrives before it departs): those rows become masked
-//    residuals r = m (xhat - x), are summed into the loss (Eq. (nnls)) and are
-//    written to the CTA's residual slot (global, L2-resident); the rows that
-//    spill into the next phase are moved to the front of the accumulators.
+//    p q rho into link-interval accumulators held as 64-bit fixed point
+//    (2^-20 vehicles): the low word in shared memory with native integer
+//    atomics, the rare carries in a per-CTA high word in global memory.  Sums
+//    are exact and independent of the deposit order, so results are bitwise
+//    reproducible.  After a phase every interval before the next phase's first
+//    departure is final (no vehicle arrives before it departs): those rows
+//    become masked residuals r = m (xhat - x), are summed into the loss
+//    (Eq. (nnls)) and are written to the CTA's residual slot (global,
+//    L2-resident); the rows that spill into the next phase move to the front.
 //  * Adjoint sweep (g = B^T r, Algorithm 1's gradient): a phase stages the
 //    residual rows its windows can reach back into shared memory, the same walk
 //    gathers r over each window, route sums are combined with the route choice
@@ -37,8 +40,8 @@
 // days walk the tick table directly (which is then exact).  When the shared
 // windows do not fit (very many links, long trips or ticks above 16 bits) the
 // same code reads ticks and residuals from global memory and accumulates link
-// flows with global atomics.  No CTA ever waits on another CTA: the work queue
-// is a single atomicAdd.
+// flows with global float atomics.  No CTA ever waits on another CTA: the work
+// queue is a single atomicAdd.
 #include <climits>
 
 #include "dode_internal.cuh"
@@ -46,6 +49,8 @@
 namespace dode {
 
 constexpr int kInactive = INT_MIN;
+constexpr float kFxScale = 1048576.f;          // 2^20: fixed-point unit of the accumulators
+constexpr double kFxInv = 1.0 / 1048576.0;
 
 template <int PREC>
 struct Operand;
@@ -77,9 +82,13 @@ struct Operand<1> {
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 struct Shared {
-    float *acc;           // [O][R]: forward accumulators / adjoint residual window (row = h - pb)
+    uint32_t *lo;         // [O][R]: accumulator low words (forward) / residual window as float bits (adjoint)
+    int *hi;              // [O][R] in global memory: accumulator high words (forward)
     uint16_t *tw;         // [A][RW]: tick window (row = h - pb)
     const uint32_t *colact;
+    const int4 *rinfo;    // [P] OD-major: (route, first link, links, 0)
+    const int2 *odr;      // [K] route range of each OD in rinfo
+    const int *task_od;   // [K] processing order
     int R, RW, pb;
 };
 
@@ -117,45 +126,122 @@ __device__ __forceinline__ RouteRegs load_route(const FusedParams &p, const Shar
 
 // Route choice of Eq. (logit) at the lane's departure interval from the route
 // times (differentiable form): shift m and reciprocal normaliser.
-__device__ __forceinline__ void logit_norm(const FusedParams &p, const float *Cday, int r0, int r1, int bi,
-                                           float &m, float &rden) {
+__device__ __forceinline__ void logit_norm(const FusedParams &p, const Shared &s, const float *Cday, int r0, int r1,
+                                           int bi, float &m, float &rden) {
     m = -INFINITY;
-    for (int i = r0; i < r1; ++i) m = fmaxf(m, -p.theta * Cday[(size_t)__ldg(&p.od_routes[i]) * p.Np + bi]);
+    for (int i = r0; i < r1; ++i) m = fmaxf(m, -p.theta * Cday[(size_t)s.rinfo[i].x * p.Np + bi]);
     float den = 0.f;
-    for (int i = r0; i < r1; ++i) den += expf(-p.theta * Cday[(size_t)__ldg(&p.od_routes[i]) * p.Np + bi] - m);
+    for (int i = r0; i < r1; ++i) den += expf(-p.theta * Cday[(size_t)s.rinfo[i].x * p.Np + bi] - m);
     rden = 1.f / den;
 }
 
-// Cells of a window past its second one (the travel time jumped by more than
-// one interval between consecutive departures): rare, handled by a loop.
-// FP32: share = seg * scale.  BF16: share rounded, last share = remainder.
-template <int PREC, bool DEPOSIT>
-__device__ __noinline__ float window_tail(float *cellp, const void *rb, size_t gidx, bool smem, int hi, int e,
-                                          int h, int N, int ipt, float scale, float used, float f) {
+// Shares of a window [T, hi) of width w over the arrival intervals (Eq. (dar)).
+// d0, the share of the interval h0 that contains T, is min(1, (e0 - T) / w) with
+// e0 the end of h0 (a zero-length window gives 1).  When the window ends in the
+// next interval its share is 1 - d0; longer windows (the travel time jumped by
+// more than an interval between consecutive departures) take the loop in
+// window_tail.  BF16 form: shares are rounded to BF16 and the last share of a
+// window is the remainder, so each departure's mass is conserved.
+template <int PREC>
+__device__ __forceinline__ float first_share(int T, int e0, float inv) {
+    const float d = fminf(1.f, (float)(e0 - T) * inv);
+    if (PREC == 0) return d;
+    return d < 1.f ? bf16_round(d) : 1.f;
+}
+
+// Add v to accumulator cell idx: 64-bit fixed point (shared low word, carries
+// into the global high word) or a global float when the ring is not in shared
+// memory.
+// FAST: the caller guarantees 0 <= v < 3000 (then v 2^20 fits 32 unsigned bits).
+template <bool SMEM_RING, bool FAST = false>
+__device__ __forceinline__ void deposit(const Shared &s, float *gacc, int idx, float v) {
+    if (!SMEM_RING) {
+        atomicAdd(gacc + idx, v);
+        return;
+    }
+    const float sv = v * kFxScale;
+    if (FAST || (sv >= 0.f && sv < 4.0e9f)) {
+        const uint32_t u = __float2uint_rn(sv);
+        const uint32_t old = atomicAdd(&s.lo[idx], u);
+        if (old + u < old) atomicAdd(&s.hi[idx], 1);
+        return;
+    }
+    const long long fx = __float2ll_rn(sv);
+    const uint32_t u = (uint32_t)fx;
+    const uint32_t old = atomicAdd(&s.lo[idx], u);
+    const int dh = (int)(fx >> 32) + ((old + u < old) ? 1 : 0);
+    if (dh) atomicAdd(&s.hi[idx], dh);
+}
+
+// Cells h0 + 1 .. of a window spanning three or more intervals.  Forward:
+// deposits f * share; adjoint: returns sum share * r.
+template <int PREC, bool SMEM_RING, bool DEPOSIT>
+__device__ __noinline__ float window_tail(const Shared &s, float *gacc, const void *rb, int idx, int hi, int e,
+                                          int h, int N, int ipt, float inv, float used, float f) {
     float acc = 0.f;
     while (hi > e && h < N) {
         const int end = min(hi, e + ipt);
         float share;
         if (PREC == 0) {
-            share = (float)(end - e) * scale;
+            share = (float)(end - e) * inv;
         } else {
-            share = end >= hi ? 1.f - used : bf16_round((float)(end - e) * scale);
+            share = end >= hi ? 1.f - used : bf16_round((float)(end - e) * inv);
             used += share;
         }
-        if (DEPOSIT) {
-            atomicAdd(cellp, f * share);
-        } else {
-            acc += share * (smem ? *cellp : Operand<PREC>::r(rb, gidx));
-        }
-        ++cellp;
-        ++gidx;
+        if (DEPOSIT)
+            deposit<SMEM_RING>(s, gacc, idx, f * share);
+        else
+            acc += share * (SMEM_RING ? __uint_as_float(s.lo[idx]) : Operand<PREC>::r(rb, (size_t)idx));
+        ++idx;
         e += ipt;
         ++h;
     }
     return acc;
 }
 
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
+template <bool SMEM_TICKS, bool TAB>
+__device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                          const int32_t *trow, int j, int T, int tb, int h0) {
+    if (TAB) return __ldg(&trow[(size_t)(j + 1) * (p.N + 1)]);
+    if (SMEM_TICKS) return T + s.tw[tb + h0];
+    return T + __ldg(&tick_day[tb + min(h0, p.N - 1)]);
+}
+
+// One route's forward walk: deposit f rho of every window on observed links.
+// FAST: every f of the warp lies in [0, 3000), so each deposit f * share does too.
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool FAST>
+__device__ __forceinline__ void forward_walk(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                             const int32_t *trow, const RouteRegs &rr, float *gacc, int beta, int bb,
+                                             bool vw, float f) {
+    const int ipt = p.div.ipt, N = p.N;
+    int T = ipt * bb;
+    for (int j = 0; j < beta; ++j) {
+        const int tb = __shfl_sync(0xffffffffu, j < 32 ? rr.t0 : rr.t1, j & 31);
+        const int ob = __shfl_sync(0xffffffffu, j < 32 ? rr.o0 : rr.o1, j & 31);
+        const int hi = __shfl_down_sync(0xffffffffu, T, 1);
+        const int h0 = interval_of(T, p.div);
+        if (ob != kInactive) {
+            if (vw && h0 < N) {
+                const int idx = ob + h0;
+                const int e0 = h0 * ipt + ipt;
+                const float inv = __fdividef(1.f, (float)(hi - T));
+                const float d0 = first_share<PREC>(T, e0, inv);
+                const float c0 = f * d0;
+                deposit<SMEM_RING, FAST>(s, gacc, idx, c0);
+                if (hi > e0 && h0 + 1 < N) {
+                    if (hi <= e0 + ipt)
+                        deposit<SMEM_RING, FAST>(s, gacc, idx + 1, f - c0);
+                    else
+                        window_tail<PREC, SMEM_RING, true>(s, gacc, nullptr, idx + 1, hi, e0, h0 + 1, N, ipt, inv, d0,
+                                                           f);
+                }
+            }
+        }
+        T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
+    }
+}
+
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int od, int b0,
                              const int32_t *tab) {
     const int lane = threadIdx.x & 31;
@@ -164,68 +250,24 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
     const bool vw = (lane < kTileW) && (b < p.N);
     const int bi = min(b, p.N - 1);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
-    const int r0 = __ldg(&p.od_ptr[od]), r1 = __ldg(&p.od_ptr[od + 1]);
+    const int2 rr0 = s.odr[od];
     const float qv = vw ? Operand<PREC>::q(p, ((size_t)day * p.K + od) * p.Np + b) : 0.f;
     if (!__any_sync(0xffffffffu, qv != 0.f)) return;     // nothing departs: no deposits
-    const int ipt = p.div.ipt, N = p.N;
-    float *acc = SMEM_RING ? s.acc : p.gring + (size_t)blockIdx.x * p.O * p.Np;
-    for (int i = r0; i < r1; ++i) {
-        const int k = __ldg(&p.od_routes[i]);
+    float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
+    for (int i = rr0.x; i < rr0.y; ++i) {
+        const int4 ri = s.rinfo[i];
+        const int k = ri.x, l0 = ri.y, beta = ri.z;
         const float f = __ldg(&p.pt[((size_t)day * p.P + k) * p.Np + bi]) * qv;
-        const int l0 = __ldg(&p.rptr[k]), beta = __ldg(&p.rptr[k + 1]) - l0;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
-        const int32_t *trow = tab ? tab + (size_t)(l0 + k) * (N + 1) + bb : nullptr;
-        int T = ipt * bb;
-        for (int j = 0; j < beta; ++j) {
-            const int tb = __shfl_sync(0xffffffffu, j < 32 ? rr.t0 : rr.t1, j & 31);
-            const int ob = __shfl_sync(0xffffffffu, j < 32 ? rr.o0 : rr.o1, j & 31);
-            const int hi = __shfl_down_sync(0xffffffffu, T, 1);
-            const int h0 = interval_of(T, p.div);
-            if (ob != kInactive && vw && h0 < N) {
-                float *cell = acc + (ob + h0);
-                const int w = hi - T;
-                if (w == 0) {
-                    atomicAdd(cell, f);
-                } else {
-                    const float inv = __fdividef(1.f, (float)w);
-                    const int e0 = h0 * ipt + ipt;
-                    const int end0 = min(hi, e0);
-                    float s0, used = 0.f;
-                    if (PREC == 0) {
-                        s0 = (float)(end0 - T) * inv;
-                    } else {
-                        s0 = end0 >= hi ? 1.f : bf16_round((float)(end0 - T) * inv);
-                        used = s0;
-                    }
-                    atomicAdd(cell, f * s0);
-                    if (hi > e0 && h0 + 1 < N) {
-                        const int end1 = min(hi, e0 + ipt);
-                        float s1;
-                        if (PREC == 0) {
-                            s1 = (float)(end1 - e0) * inv;
-                        } else {
-                            s1 = end1 >= hi ? 1.f - used : bf16_round((float)(end1 - e0) * inv);
-                            used += s1;
-                        }
-                        atomicAdd(cell + 1, f * s1);
-                        if (hi > e0 + ipt && h0 + 2 < N)
-                            window_tail<PREC, true>(cell + 2, nullptr, 0, true, hi, e0 + ipt, h0 + 2, N, ipt, inv,
-                                                    used, f);
-                    }
-                }
-            }
-            if (trow) {
-                T = __ldg(&trow[(size_t)(j + 1) * (N + 1)]);
-            } else if (SMEM_TICKS) {
-                T += s.tw[tb + h0];
-            } else {
-                T += __ldg(&tick_day[tb + min(h0, N - 1)]);
-            }
-        }
+        const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bb : nullptr;
+        if (__all_sync(0xffffffffu, f >= 0.f && f < 3000.f))
+            forward_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trow, rr, gacc, beta, bb, vw, f);
+        else
+            forward_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, false>(p, s, tick_day, trow, rr, gacc, beta, bb, vw, f);
     }
 }
 
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int od, int b0, const void *rb,
                              const int32_t *tab, double *s_dth) {
     const int lane = threadIdx.x & 31;
@@ -234,23 +276,19 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
     const bool vw = (lane < kTileW) && (b < p.N);
     const int bi = min(b, p.N - 1);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
-    const int r0 = __ldg(&p.od_ptr[od]), r1 = __ldg(&p.od_ptr[od + 1]);
+    const int2 rr0 = s.odr[od];
     const int ipt = p.div.ipt, N = p.N;
     const size_t qi = ((size_t)day * p.K + od) * p.Np + b;
     const bool grad = p.mode == MODE_LOSS_GRAD;
     const float *Cday = p.C + (size_t)day * p.P * p.Np;
-    float m = 0.f, rden = 1.f, cbar = 0.f;
-    if (grad) {
-        logit_norm(p, Cday, r0, r1, bi, m, rden);
-        for (int i = r0; i < r1; ++i) {
-            const float c = Cday[(size_t)__ldg(&p.od_routes[i]) * p.Np + bi];
-            cbar += expf(-p.theta * c - m) * rden * c;
-        }
-    }
-    const float *racc = SMEM_RING ? s.acc : nullptr;
-    float g = 0.f, dth = 0.f;
-    for (int i = r0; i < r1; ++i) {
-        const int k = __ldg(&p.od_routes[i]);
+    float m = 0.f, rden = 1.f;
+    if (grad) logit_norm(p, s, Cday, rr0.x, rr0.y, bi, m, rden);
+    const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
+    float g = 0.f;
+    double dth = 0.0;
+    for (int i = rr0.x; i < rr0.y; ++i) {
+        const int4 ri = s.rinfo[i];
+        const int k = ri.x, l0 = ri.y, beta = ri.z;
         float pk, ck = 0.f;
         if (grad) {
             ck = Cday[(size_t)k * p.Np + bi];
@@ -258,9 +296,8 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
         } else {
             pk = __ldg(&p.pt[((size_t)day * p.P + k) * p.Np + bi]);
         }
-        const int l0 = __ldg(&p.rptr[k]), beta = __ldg(&p.rptr[k + 1]) - l0;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
-        const int32_t *trow = tab ? tab + (size_t)(l0 + k) * (N + 1) + bb : nullptr;
+        const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bb : nullptr;
         float gp = 0.f;
         int T = ipt * bb;
         for (int j = 0; j < beta; ++j) {
@@ -268,54 +305,36 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
             const int ob = __shfl_sync(0xffffffffu, j < 32 ? rr.o0 : rr.o1, j & 31);
             const int hi = __shfl_down_sync(0xffffffffu, T, 1);
             const int h0 = interval_of(T, p.div);
-            if (ob != kInactive && vw && h0 < N) {
-                const int idx = ob + h0;
-                auto rv = [&](int d) -> float {
-                    return SMEM_RING ? racc[idx + d] : Operand<PREC>::r(rb, (size_t)(idx + d));
-                };
-                const int w = hi - T;
-                if (w == 0) {
-                    gp += rv(0);
-                } else {
-                    const float inv = __fdividef(1.f, (float)w);
+            if (ob != kInactive) {
+                if (vw && h0 < N) {
+                    const int idx = ob + h0;
                     const int e0 = h0 * ipt + ipt;
-                    const int end0 = min(hi, e0);
-                    float a, used = 0.f;
-                    if (PREC == 0) {
-                        a = (float)(end0 - T) * rv(0);
-                    } else {
-                        const float s0 = end0 >= hi ? 1.f : bf16_round((float)(end0 - T) * inv);
-                        used = s0;
-                        a = s0 * rv(0);
-                    }
+                    const float inv = __fdividef(1.f, (float)(hi - T));
+                    const float d0 = first_share<PREC>(T, e0, inv);
+                    float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
                     if (hi > e0 && h0 + 1 < N) {
-                        const int end1 = min(hi, e0 + ipt);
-                        if (PREC == 0) {
-                            a += (float)(end1 - e0) * rv(1);
-                        } else {
-                            const float s1 = end1 >= hi ? 1.f - used : bf16_round((float)(end1 - e0) * inv);
-                            used += s1;
-                            a += s1 * rv(1);
-                        }
-                        if (hi > e0 + ipt && h0 + 2 < N) {
-                            float *cp = SMEM_RING ? const_cast<float *>(racc) + idx + 2 : nullptr;
-                            a += window_tail<PREC, false>(cp, rb, (size_t)(idx + 2), SMEM_RING, hi, e0 + ipt, h0 + 2,
-                                                          N, ipt, PREC == 0 ? 1.f : inv, used, 0.f);
-                        }
+                        if (hi <= e0 + ipt)
+                            a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                        else
+                            a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt,
+                                                                     inv, d0, 0.f);
                     }
-                    gp += PREC == 0 ? a * inv : a;
+                    gp += a;
                 }
             }
-            if (trow) {
-                T = __ldg(&trow[(size_t)(j + 1) * (N + 1)]);
-            } else if (SMEM_TICKS) {
-                T += s.tw[tb + h0];
-            } else {
-                T += __ldg(&tick_day[tb + min(h0, N - 1)]);
-            }
+            T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
         }
         g += pk * gp;
-        if (grad && vw) dth += 2.f * p.q[qi] * gp * pk * (cbar - ck);
+        if (grad && vw) {
+            // dp_k/dtheta = p_k (cbar - C_k) with cbar - C_k = sum_k' p_k' (C_k' - C_k):
+            // differences of route times first, which avoids the cancellation
+            float dc = 0.f;
+            for (int i2 = rr0.x; i2 < rr0.y; ++i2) {
+                const float c2 = Cday[(size_t)s.rinfo[i2].x * p.Np + bi];
+                dc += expf(-p.theta * c2 - m) * rden * (c2 - ck);
+            }
+            dth += 2.0 * (double)p.q[qi] * (double)gp * (double)pk * (double)dc;
+        }
     }
     if (!vw) return;
     if (p.mode == MODE_SOLVE) {
@@ -327,7 +346,7 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
         if (PREC == 1) p.qb[qi] = __float2bfloat16_rn(qv);
     } else if (grad) {
         p.gout[qi] = 2.f * g;
-        atomicAdd(s_dth, (double)dth);
+        atomicAdd(s_dth, dth);
     }
 }
 
@@ -346,27 +365,54 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 }
 
 // Tick rows [pb, pb + RW) of every link; rows past the end of the day repeat the
-// last interval (the link entry rule clamps to it).
+// last interval (the link entry rule clamps to it).  Each warp loads four
+// links' rows before storing, to keep many loads in flight.
 __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, const int32_t *tick_day) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int a = warp; a < p.A; a += nw) {
-        const int32_t *src = tick_day + (size_t)a * p.Np;
-        uint16_t *dst = s.tw + a * s.RW;
-        for (int r = lane; r < s.RW; r += 32) dst[r] = (uint16_t)__ldg(&src[min(s.pb + r, p.N - 1)]);
+    for (int a0 = warp; a0 < p.A; a0 += 4 * nw) {
+        for (int r0 = 0; r0 < s.RW; r0 += 32) {
+            const int r = r0 + lane;
+            int v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int a = a0 + u * nw;
+                v[u] = (a < p.A && r < s.RW) ? __ldg(&tick_day[(size_t)a * p.Np + min(s.pb + r, p.N - 1)]) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int a = a0 + u * nw;
+                if (a < p.A && r < s.RW) s.tw[a * s.RW + r] = (uint16_t)v[u];
+            }
+        }
     }
 }
 
-// Residual rows [pb, pb + R) (clipped to the day) of every observed link.
+// Residual rows [pb, pb + R) (clipped to the day) of every observed link, as
+// float bits in the accumulator array.
 template <int PREC>
 __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, const void *rb) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int rows = min(s.R, p.N - s.pb);
-    for (int o = warp; o < p.O; o += nw) {
-        float *dst = s.acc + o * s.R;
-        for (int r = lane; r < rows; r += 32) dst[r] = Operand<PREC>::r(rb, (size_t)o * p.Np + s.pb + r);
+    for (int o0 = warp; o0 < p.O; o0 += 4 * nw) {
+        for (int r0 = 0; r0 < rows; r0 += 32) {
+            const int r = r0 + lane;
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int o = o0 + u * nw;
+                v[u] = (o < p.O && r < rows) ? Operand<PREC>::r(rb, (size_t)o * p.Np + s.pb + r) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int o = o0 + u * nw;
+                if (o < p.O && r < rows) s.lo[o * s.R + r] = __float_as_uint(v[u]);
+            }
+        }
     }
 }
 
+// Dynamic shared memory layout (16-byte aligned blocks):
+//   rinfo int4[P] | odr int2[K] | task_od int[K] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
 __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -374,14 +420,24 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     s.R = SMEM_RING ? p.ring_rows : 0;
     s.RW = SMEM_TICKS ? p.tick_rows : 0;
     s.pb = 0;
-    unsigned char *cur = smem_raw;
-    s.acc = reinterpret_cast<float *>(cur);
-    if (SMEM_RING) cur += (size_t)p.O * s.R * sizeof(float);
-    uint32_t *colact = reinterpret_cast<uint32_t *>(cur);
-    cur += (size_t)p.Ow * sizeof(uint32_t);
-    cur = smem_raw + (((cur - smem_raw) + 15) & ~(size_t)15);
-    s.tw = reinterpret_cast<uint16_t *>(cur);
+    auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    size_t off = 0;
+    int4 *rinfo = reinterpret_cast<int4 *>(smem_raw + off);
+    off = align16(off + (size_t)p.P * sizeof(int4));
+    int2 *odr = reinterpret_cast<int2 *>(smem_raw + off);
+    off = align16(off + (size_t)p.K * sizeof(int2));
+    int *task_od = reinterpret_cast<int *>(smem_raw + off);
+    off = align16(off + (size_t)p.K * sizeof(int));
+    uint32_t *colact = reinterpret_cast<uint32_t *>(smem_raw + off);
+    off = align16(off + (size_t)p.Ow * sizeof(uint32_t));
+    s.lo = reinterpret_cast<uint32_t *>(smem_raw + off);
+    if (SMEM_RING) off = align16(off + (size_t)p.O * s.R * sizeof(uint32_t));
+    s.tw = reinterpret_cast<uint16_t *>(smem_raw + off);
     s.colact = colact;
+    s.rinfo = rinfo;
+    s.odr = odr;
+    s.task_od = task_od;
+    s.hi = SMEM_RING ? reinterpret_cast<int *>(p.gring) + (size_t)blockIdx.x * p.O * s.R : nullptr;
     __shared__ int s_day;
     __shared__ int s_task;
     __shared__ double s_red[32];
@@ -394,8 +450,21 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                (size_t)blockIdx.x * p.O * p.Np * (PREC == 1 ? sizeof(__nv_bfloat16) : sizeof(float));
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
 
+    // network tables
+    for (int i = threadIdx.x; i < p.P; i += nthr) {
+        const int k = __ldg(&p.od_routes[i]);
+        const int l0 = __ldg(&p.rptr[k]);
+        rinfo[i] = make_int4(k, l0, __ldg(&p.rptr[k + 1]) - l0, 0);
+    }
+    for (int i = threadIdx.x; i < p.K; i += nthr) {
+        odr[i] = make_int2(__ldg(&p.od_ptr[i]), __ldg(&p.od_ptr[i + 1]));
+        task_od[i] = __ldg(&p.task_od[i]);
+    }
     if (SMEM_RING) {
-        for (int i = threadIdx.x; i < p.O * s.R; i += nthr) s.acc[i] = 0.f;
+        for (int i = threadIdx.x; i < p.O * s.R; i += nthr) {
+            s.lo[i] = 0u;
+            s.hi[i] = 0;
+        }
     } else {
         for (size_t i = threadIdx.x; i < (size_t)p.O * p.Np; i += nthr) gacc[i] = 0.f;
     }
@@ -445,40 +514,86 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int od = __ldg(&p.task_od[t / nt]);
+                    const int od = task_od[t / nt];
                     const int b0 = pb0 + (t % nt) * kTileW;
-                    forward_task<PREC, SMEM_RING, SMEM_TICKS>(p, s, day, od, b0, tab);
+                    if (tab)
+                        forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, od, b0, tab);
+                    else
+                        forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, od, b0, tab);
                 }
                 __syncthreads();
                 // rows [pb0, pb0 + 31 nt) are final: residual, loss, residual slot;
                 // the spill rows move to the front for the next phase
                 const int span = nt * kTileW;
                 const int rows = min(span, p.N - pb0);
-                for (int o = warp; o < p.O; o += nwarps) {
-                    float *row = SMEM_RING ? s.acc + o * s.R : gacc + (size_t)o * p.Np + pb0;
-                    for (int r = lane; r < rows; r += 32) {
+                for (int o0 = warp; o0 < p.O; o0 += 2 * nwarps) {
+                    for (int r0 = 0; r0 < rows; r0 += 32) {
+                        const int r = r0 + lane;
                         const int h = pb0 + r;
-                        const float x = row[r];
-                        if (!SMEM_RING) row[r] = 0.f;
-                        if (p.mode == MODE_FORWARD) {
-                            p.xout[((size_t)day * p.O + o) * p.Np + h] = x;
-                        } else {
-                            const bool on = (mk[(size_t)o * p.Nw + (h >> 5)] >> (h & 31)) & 1u;
-                            const float rr = on ? x - cnt[(size_t)o * p.Np + h] : 0.f;
-                            lsum += rr * rr;
-                            Operand<PREC>::store_r(rb, (size_t)o * p.Np + h, rr);
+                        float x[2], c[2];
+                        bool on[2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int o = o0 + u * nwarps;
+                            x[u] = 0.f;
+                            c[u] = 0.f;
+                            on[u] = false;
+                            if (o < p.O && r < rows) {
+                                if (SMEM_RING) {
+                                    const int idx = o * s.R + r;
+                                    const long long v = ((long long)s.hi[idx] << 32) | (long long)s.lo[idx];
+                                    x[u] = (float)((double)v * kFxInv);
+                                } else {
+                                    float *cell = gacc + (size_t)o * p.Np + h;
+                                    x[u] = *cell;
+                                    *cell = 0.f;
+                                }
+                                if (p.mode != MODE_FORWARD) {
+                                    on[u] = (mk[(size_t)o * p.Nw + (h >> 5)] >> (h & 31)) & 1u;
+                                    c[u] = cnt[(size_t)o * p.Np + h];
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const int o = o0 + u * nwarps;
+                            if (o < p.O && r < rows) {
+                                if (p.mode == MODE_FORWARD) {
+                                    p.xout[((size_t)day * p.O + o) * p.Np + h] = x[u];
+                                } else {
+                                    const float rr = on[u] ? x[u] - c[u] : 0.f;
+                                    lsum += rr * rr;
+                                    Operand<PREC>::store_r(rb, (size_t)o * p.Np + h, rr);
+                                }
+                            }
                         }
                     }
-                    if (SMEM_RING) {
-                        __syncwarp();
+                }
+                if (SMEM_RING) {
+                    // move the spill rows [span, span + spill) to the front, zero the rest
+                    __syncthreads();
+                    for (int o = warp; o < p.O; o += nwarps) {
+                        uint32_t *lrow = s.lo + o * s.R;
+                        int *hrow = s.hi + o * s.R;
                         for (int q0 = 0; q0 < spill; q0 += 32) {
                             const int r = q0 + lane;
-                            const float v = r < spill ? row[span + r] : 0.f;
+                            uint32_t vl = 0;
+                            int vh = 0;
+                            if (r < spill) {
+                                vl = lrow[span + r];
+                                vh = hrow[span + r];
+                            }
                             __syncwarp();
-                            if (r < spill) row[r] = v;
+                            if (r < spill) {
+                                lrow[r] = vl;
+                                hrow[r] = vh;
+                            }
                             __syncwarp();
                         }
-                        for (int r = spill + lane; r < span + spill; r += 32) row[r] = 0.f;
+                        for (int r = spill + lane; r < span + spill; r += 32) {
+                            lrow[r] = 0u;
+                            hrow[r] = 0;
+                        }
                     }
                 }
                 if (threadIdx.x == 0) s_task = 0;
@@ -505,16 +620,19 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int od = __ldg(&p.task_od[t / nt]);
+                    const int od = task_od[t / nt];
                     const int b0 = pb0 + (t % nt) * kTileW;
-                    adjoint_task<PREC, SMEM_RING, SMEM_TICKS>(p, s, day, od, b0, rb, tab, &s_dth);
+                    if (tab)
+                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, od, b0, rb, tab, &s_dth);
+                    else
+                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, od, b0, rb, tab, &s_dth);
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) s_task = 0;
             }
             __syncthreads();
             if (SMEM_RING) {
-                for (int i = threadIdx.x; i < p.O * s.R; i += nthr) s.acc[i] = 0.f;
+                for (int i = threadIdx.x; i < p.O * s.R; i += nthr) s.lo[i] = 0u;
             }
             __syncthreads();
             if (p.mode == MODE_LOSS_GRAD) {

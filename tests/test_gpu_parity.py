@@ -169,12 +169,12 @@ def test_loss_grad_parity(c1, theta):
     np.testing.assert_allclose(loss_only, loss, rtol=1e-6)
     for d in range(w.n_days):
         day = net.day(sp[d], theta=theta)
-        lo, dqo, dtho = day.loss_grad(counts[d], mask[d], q[d].astype(np.float64))
+        lo, dqo, dtho, dabs = day.loss_grad(counts[d], mask[d], q[d].astype(np.float64), with_scale=True)
         assert loss[d] == pytest.approx(lo, rel=1e-5)
         assert rel_norm(dq[d], dqo) < 1e-4
-        if theta == 0.0 and abs(dtho) < 1e-9:
-            continue
-        assert dth[d] == pytest.approx(dtho, rel=1e-4, abs=1e-6 * abs(lo))
+        # dL/dtheta is a sum of terms of both signs; FP32 rounding is measured
+        # against the sum of their magnitudes
+        assert abs(dth[d] - dtho) <= 1e-5 * dabs, (dth[d], dtho, dabs)
 
 
 # ---------------------------------------------------------------------------
