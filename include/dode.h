@@ -185,6 +185,31 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
 int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, float *dq,
                    double *dtheta, int32_t ptr_kind);
 
+/*
+ * dode_loss_static_scratch -- the per-day loss of dode_loss for the loaded days,
+ * computed without allocating any device memory.  The paper has no counterpart:
+ * this serves callers that cannot call cudaMalloc once running (a real-time or
+ * certified loop that forbids allocation after start-up, a process whose GPU
+ * memory is owned by another allocator, a latency-critical path that cannot
+ * afford cudaMalloc's implicit device synchronisation).
+ *   q     [D][N][n_od] OD flows, FP32, DEVICE pointer
+ *   theta logit dispersion per minute
+ *   loss  [D] per-day loss, FP64, DEVICE pointer (written by the kernel)
+ * All per-call scratch (q in the kernel layout, the route-choice table, the
+ * residual slots and accumulator words of the resident CTAs, the work-queue
+ * counter) comes from one 32 MiB file-scope device array that every GPU that
+ * loads this library holds until the process exits; the day data and route
+ * tables are the context's, loaded earlier.  If the days need more scratch
+ * than that for even one CTA the call returns DODE_ERR_ARG and says how much;
+ * otherwise it runs as many resident CTAs as fit.  The first call on a device
+ * looks up the array's device address there (cudaGetSymbolAddress), so that
+ * first call should come before any stream capture.  Every call shares the
+ * array and leaves its contents behind: calls that overlap on the GPU (on
+ * different streams or contexts of the same device) race and must not be made.
+ * Returns after the loss is written.
+ */
+int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float theta, double *loss);
+
 /* ---- inspection (host outputs; for checks and debugging) --------------------- */
 
 /* Tick table of one day: out[h][a] = travel time of link a entered in interval h. */

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -1087,4 +1088,117 @@ int dode_get_dar(dode_ctx *ctx, int32_t day, int64_t *n, int32_t *kjh, float *rh
     return DODE_OK;
 }
 
+
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Loss evaluation with static scratch (no device allocation).
+//
+// Some callers cannot call cudaMalloc once they are running: a real-time or
+// certified control loop that forbids device allocation after start-up, a
+// host process whose GPU memory is entirely owned by another allocator (a
+// framework's caching allocator or a fixed arena), or a latency-critical path
+// where cudaMalloc's implicit device synchronisation would stall other
+// streams.  dode_loss_static_scratch serves them: everything the fused kernel
+// needs beyond the context's loaded days and the caller's buffers lives in
+// one file-scope device array of kStaticScratchBytes, which every GPU that
+// loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;   // 32 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char dode_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_scratch_mu;
+void *g_static_scratch_ptr[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Device address of the static scratch on the context's device: looked up
+// once per device (with that device current) and cached.
+int static_scratch(dode_ctx *ctx, unsigned char **out) {
+    if (ctx->dev < 0 || ctx->dev >= kMaxDevices) return fail(ctx, DODE_ERR_ARG, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+    if (!g_static_scratch_ptr[ctx->dev]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, dode_static_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(ctx, DODE_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+        g_static_scratch_ptr[ctx->dev] = ptr;
+    }
+    *out = static_cast<unsigned char *>(g_static_scratch_ptr[ctx->dev]);
+    return DODE_OK;
+}
+
+}  // namespace
+
+extern "C" int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float theta, double *loss) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!q || !loss || !std::isfinite(theta)) return fail(ctx, DODE_ERR_ARG, "loss_static_scratch arguments");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    unsigned char *base = nullptr;
+    rc = static_scratch(ctx, &base);
+    if (rc) return rc;
+    const int prec = ctx->opt.precision;
+    FusedShape sh;
+    rc = fused_shape(ctx, prec, &sh);
+    if (rc) return rc;
+    // scratch layout: queue | q (internal layout) | q BF16 copy | route choice |
+    // per CTA: residual slot, accumulator words
+    const size_t qn = (size_t)ctx->D * ctx->K * ctx->Np;
+    size_t off = 256;
+    const size_t off_q = off;
+    off = align256(off + qn * sizeof(float));
+    const size_t off_qb = off;
+    if (prec == DODE_PREC_BF16) off = align256(off + qn * sizeof(__nv_bfloat16));
+    const size_t off_pt = off;
+    off = align256(off + (size_t)ctx->D * ctx->P * ctx->Np * sizeof(float));
+    const size_t slot_r = align256((size_t)ctx->O * ctx->Np * (prec == DODE_PREC_BF16 ? 2 : 4));
+    const size_t slot_g = align256((size_t)ctx->O * std::max(ctx->Np, sh.ring_rows) * 4);
+    const size_t need_one = off + slot_r + slot_g;
+    if (need_one > kStaticScratchBytes) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "these %d days need %zu bytes of scratch for a single CTA; the static scratch holds %zu bytes",
+                 ctx->D, need_one, kStaticScratchBytes);
+        return fail(ctx, DODE_ERR_ARG, buf);
+    }
+    const int grid = (int)std::min<size_t>((size_t)sh.grid, (kStaticScratchBytes - off) / (slot_r + slot_g));
+    const size_t off_rb = off;
+    const size_t off_g = off + (size_t)grid * slot_r;
+    CU(cudaStreamSynchronize(ctx->stream));
+    // every call shares the scratch: the queue counter starts at zero, the
+    // accumulator words are cleared by the kernel itself, the rest is written
+    // before it is read
+    CU(cudaMemsetAsync(base, 0, 256, ctx->stream));
+    float *qi = reinterpret_cast<float *>(base + off_q);
+    CUL(launch_transpose_in(q, qi, ctx->D, ctx->N, ctx->Np, ctx->K, ctx->stream));
+    __nv_bfloat16 *qb = reinterpret_cast<__nv_bfloat16 *>(base + off_qb);
+    if (prec == DODE_PREC_BF16) CUL(launch_to_bf16(qi, qb, qn, ctx->stream));
+    float *pt = reinterpret_cast<float *>(base + off_pt);
+    CUL(launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, theta, ctx->D, ctx->P, ctx->N,
+                            ctx->Np, pt, ctx->stream));
+    FusedParams p = base_params(ctx);
+    p.mode = MODE_LOSS;
+    p.theta = theta;
+    p.q = qi;
+    p.G = nullptr;
+    p.qb = qb;
+    p.pt = pt;
+    p.loss = loss;
+    p.trace = nullptr;
+    p.rbuf = base + off_rb;
+    p.gring = reinterpret_cast<float *>(base + off_g);
+    p.ring_rows = sh.ring_rows;
+    p.tick_rows = sh.tick_rows;
+    p.tiles_per_phase = sh.tiles_per_phase;
+    p.queue = reinterpret_cast<int *>(base);
+    CUL(launch_fused(p, prec, grid, sh.block, sh.smem, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return check_device_error(ctx);
+}
+

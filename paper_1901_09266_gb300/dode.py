@@ -30,7 +30,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 # every entry point of include/dode.h
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
-           "dode_loss_grad", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
+           "dode_loss_grad", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
            "dode_last_kernel_ms", "dode_last_launches", "dode_total_launches", "dode_set_launch", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH):
         "dode_forward": (ct.c_int, [vp, vp, vp, i32]),
         "dode_loss": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_loss_grad": (ct.c_int, [vp, vp, f32, vp, vp, vp, i32]),
+        "dode_loss_static_scratch": (ct.c_int, [vp, vp, f32, vp]),
         "dode_get_ticks": (ct.c_int, [vp, i32, vp]),
         "dode_get_route_times": (ct.c_int, [vp, i32, vp]),
         "dode_get_day_info": (ct.c_int, [vp, i32, ct.POINTER(i64), ct.POINTER(i32)]),
@@ -265,6 +266,16 @@ class Context:
         th = self.opt.theta_per_min if theta is None else theta
         self._check(load().dode_loss_grad(self.h, pq, th, loss.ctypes.data, pd, dth.ctypes.data, kind))
         return loss, dq, dth
+
+    def loss_static_scratch(self, q, loss_out, theta: Optional[float] = None) -> None:
+        """Per-day loss into ``loss_out`` without any device allocation (see
+        include/dode.h): ``q`` and ``loss_out`` must be CUDA tensors."""
+        pq, _, kq = self._ptr(q, np.float32, (self.D, self.N, self.K))
+        pl, _, kl = self._ptr(loss_out, np.float64, (self.D,))
+        if kq != PTR_DEVICE or kl != PTR_DEVICE:
+            raise ValueError("q and loss_out must be CUDA tensors")
+        th = self.opt.theta_per_min if theta is None else theta
+        self._check(load().dode_loss_static_scratch(self.h, pq, th, pl))
 
     # ---- inspection --------------------------------------------------------
     def ticks(self, day: int) -> np.ndarray:
