@@ -46,6 +46,28 @@ def shard_days(n_days: int, rank: int, world: int) -> list:
     return list(range(rank * n_days, (rank + 1) * n_days))
 
 
+def measured_traffic(workload: str, precision: str):
+    """DRAM bytes per day-iteration of the fused kernel from the committed ncu
+    summary, if it was taken of this workload, this precision and the current
+    kernel source (matched by hash); else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "fused_kernel_corridor-3yr-152d_traffic.txt")
+    try:
+        rec = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+        src = open(os.path.join(ROOT, "paper_1901_09266_gb300", "csrc", "fused.cu"), "rb").read()
+    except OSError:
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("fused_cu_sha256_16"):
+        return None
+    if workload != "corridor-3yr" or precision != "bf16" or "BF16" not in rec.get("kernel", ""):
+        return None
+    return float(rec["bytes_per_day_iteration"])
+
+
 def _peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -240,11 +262,17 @@ def run_gpu(args):
     days = shard_days(w.n_days, rank, world)
     prec = dode.PREC_BF16 if args.precision == "bf16" else dode.PREC_FP32
     form = dode.FORM_PLAIN if args.form == "plain" else dode.FORM_FUSED
-    ctx = dode.Context.from_workload(w, form=form, precision=prec)
+    ctx = dode.Context.from_workload(w, form=form, precision=prec, use_graph=1 if args.graph else 0)
     ctx.use_torch_stream()
-    if args.block or args.ctas:
-        ctx.set_launch(args.block, args.ctas)
     sp, counts, mask = gpu_inputs(w, days)
+    tuned = None
+    if args.autotune:
+        from paper_1901_09266_gb300 import autotune
+        ctx.set_days(counts, sp, mask)
+        tuned = autotune.tune(ctx, iters=3, step=args.step)
+        tuned = {k: tuned[k] for k in ("block", "ctas_per_sm", "max_ctas", "ms", "cached")}
+    elif args.block or args.ctas:
+        ctx.set_launch(args.block, args.ctas)
     D, N, K, O, A = len(days), w.n_intervals, w.routes.n_od, w.net.n_obs, w.net.n_links
     # device-resident inputs and outputs
     sp_d = torch.from_numpy(sp).to(dev)
@@ -316,8 +344,15 @@ def run_gpu(args):
     kms = float(np.mean(kern_ms))
     achieved = per_unit * D * E / (kms / 1e3) / 1e9
     peak = peaks.get("hbm_gbs")
+    traffic, traffic_src = args.traffic, "command line" if args.traffic is not None else None
+    if traffic is None and form == dode.FORM_FUSED:
+        per = measured_traffic(w.name, args.precision)
+        if per is not None:
+            traffic = per * D * E
+            traffic_src = ("ncu dram__bytes_read+write of a 152-day, 2-epoch capture of this kernel, "
+                           "scaled by day-iterations (profiles/fused_kernel_corridor-3yr-152d_traffic.txt)")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak if peak else 6800.0, "unit": "GB/s",
-            "frac": achieved / (peak if peak else 6800.0), "traffic": args.traffic,
+            "frac": achieved / (peak if peak else 6800.0), "traffic": traffic, "traffic_source": traffic_src,
             "peak_source": "measured" if peak else "fallback", "bytes_per_unit": per_unit,
             "kernel_ms": kms}
 
@@ -366,7 +401,8 @@ def run_gpu(args):
             "dtype": "bf16" if prec == dode.PREC_BF16 else "f32", "data": "synthetic",
             "config": {"workload": w.name, "days_per_gpu": D, "intervals": N, "od_pairs": K,
                        "routes": w.routes.n_routes, "links": A, "detectors": O, "epochs_per_step": E,
-                       "form": args.form, "precision": args.precision,
+                       "form": args.form, "precision": args.precision, "graph": bool(args.graph),
+                       "launch": tuned or {"block": args.block, "ctas_per_sm": args.ctas},
                        "l2": "inputs larger than L2 (reloaded every step)"},
             "e2e": {"value": e2e_value, "unit": "day-iter/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
@@ -400,10 +436,12 @@ def main(argv=None):
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
+    ap.add_argument("--graph", action="store_true", help="replay the solve as a CUDA graph")
+    ap.add_argument("--autotune", action="store_true", help="pick the launch shape with the autotuner")
     ap.add_argument("--compare-epochs", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-days", type=int, default=64)
-    ap.add_argument("--ref-epochs", type=int, default=10)
+    ap.add_argument("--ref-days", type=int, default=128)
+    ap.add_argument("--ref-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused launch from an ncu capture of the same kernel")

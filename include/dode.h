@@ -107,6 +107,10 @@ typedef struct {
     int32_t ctas_per_sm;     /* fused kernel CTAs per SM (0 = tuned default) */
     int32_t device;          /* CUDA device ordinal (-1 = current) */
     void *stream;            /* cudaStream_t for all work (NULL = default stream) */
+    int32_t use_graph;       /* 1: dode_solve with DEVICE outputs replays a CUDA graph of its device
+                                work (captured on first use, re-captured when iters, step, theta or
+                                the launch shape change) */
+    int32_t max_ctas;        /* cap on resident CTAs of the fused kernel (0 = as many as fit) */
 } dode_options;
 
 typedef struct dode_ctx dode_ctx;
@@ -237,6 +241,9 @@ int64_t dode_last_launches(const dode_ctx *ctx);
 int64_t dode_total_launches(const dode_ctx *ctx);
 /* Override the fused kernel launch shape (autotuner); 0 = tuned default. */
 int dode_set_launch(dode_ctx *ctx, int32_t block_threads, int32_t ctas_per_sm);
+/* Cap the fused kernel's resident CTAs (0 = as many as fit); results do not
+ * depend on it (each day is solved by one CTA, sums are exact). */
+int dode_set_max_ctas(dode_ctx *ctx, int32_t max_ctas);
 /* Switch stream (cudaStream_t); the context's previous work must be complete. */
 int dode_set_stream(dode_ctx *ctx, void *stream);
 

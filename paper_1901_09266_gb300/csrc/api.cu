@@ -74,10 +74,26 @@ struct dode_ctx {
     double last_ms = 0.0;
     int64_t last_launches = 0;
     int64_t total_launches = 0;
+    // CUDA graph of dode_solve's device work (use_graph)
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t own_stream = nullptr;     // capture stream when the context uses the legacy default stream
+    struct GraphKey {
+        int iters = -1, grid = 0, block = 0, ring = 0, tick = 0, F = 0, prec = -1;
+        float step = 0.f, theta = 0.f;
+        const void *q_out = nullptr, *loss_out = nullptr;
+        size_t smem = 0;
+        bool operator==(const GraphKey &o) const {
+            return iters == o.iters && grid == o.grid && block == o.block && ring == o.ring && tick == o.tick &&
+                   F == o.F && prec == o.prec && step == o.step && theta == o.theta && q_out == o.q_out &&
+                   loss_out == o.loss_out && smem == o.smem;
+        }
+    } graph_key;
     std::string err;
 };
 
 namespace {
+
+void drop_graph(dode_ctx *ctx);
 
 int fail(dode_ctx *c, int code, const std::string &msg) {
     if (c) c->err = msg;
@@ -268,6 +284,7 @@ int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
     occ = std::min(occ, per_sm);
     s->block = block;
     s->grid = std::max(1, std::min(ctx->D, ctx->n_sm * occ));
+    if (ctx->opt.max_ctas > 0) s->grid = std::min(s->grid, ctx->opt.max_ctas);
     s->ring_rows = R;
     s->tick_rows = RW;
     s->tiles_per_phase = F;
@@ -279,6 +296,7 @@ int ensure_slots(dode_ctx *ctx, const FusedShape &s, int precision) {
     const size_t elems = (size_t)s.grid * ctx->O * ctx->Np;
     const size_t rb = elems * (precision == DODE_PREC_BF16 ? 2 : 4);
     if (rb > ctx->rbuf_bytes) {
+        drop_graph(ctx);
         if (ctx->d_rbuf) cudaFree(ctx->d_rbuf);
         ctx->d_rbuf = nullptr;
         ctx->rbuf_bytes = 0;
@@ -288,6 +306,7 @@ int ensure_slots(dode_ctx *ctx, const FusedShape &s, int precision) {
     // global accumulators (no shared ring) or the accumulators' high words
     const size_t gelems = (size_t)s.grid * ctx->O * std::max(ctx->Np, s.ring_rows);
     if (gelems * 4 > ctx->gring_bytes) {
+        drop_graph(ctx);
         dfree(ctx->d_gring);
         ctx->gring_bytes = 0;
         CU(cudaMalloc(&ctx->d_gring, gelems * 4));
@@ -365,7 +384,14 @@ int finish_timing(dode_ctx *ctx) {
     return DODE_OK;
 }
 
+void drop_graph(dode_ctx *ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    ctx->graph_key = dode_ctx::GraphKey();
+}
+
 void free_days(dode_ctx *ctx) {
+    drop_graph(ctx);
     dfree(ctx->d_ticks);
     dfree(ctx->d_counts);
     dfree(ctx->d_mask);
@@ -439,9 +465,86 @@ int plain_prepare(dode_ctx *ctx, float theta, PlainParams *pp) {
     return DODE_OK;
 }
 
+// Fused solve as a CUDA graph: route choice, queue reset, the persistent
+// kernel (between the timing events) and the copies to the caller's device
+// buffers are captured once and replayed while iters, step, theta, the launch
+// shape and the output pointers stay the same.
+int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_out, double *loss_out) {
+    const int prec = ctx->opt.precision;
+    FusedShape s;
+    int rc = fused_shape(ctx, prec, &s);
+    if (rc) return rc;
+    rc = ensure_slots(ctx, s, prec);
+    if (rc) return rc;
+    CU(fused_set_attr(s.ring_rows > 0, s.tick_rows > 0, prec, s.smem));
+    dode_ctx::GraphKey key;
+    key.iters = iters;
+    key.grid = s.grid;
+    key.block = s.block;
+    key.ring = s.ring_rows;
+    key.tick = s.tick_rows;
+    key.F = s.tiles_per_phase;
+    key.prec = prec;
+    key.step = step;
+    key.theta = ctx->opt.theta_per_min;
+    key.q_out = q_out;
+    key.loss_out = loss_out;
+    key.smem = s.smem;
+    if (!ctx->stream && !ctx->own_stream) CU(cudaStreamCreate(&ctx->own_stream));
+    cudaStream_t gs = ctx->stream ? ctx->stream : ctx->own_stream;
+    int64_t kernels = 3 + (prec == DODE_PREC_BF16 ? 1 : 0) + (q_out ? 1 : 0);
+    if (!ctx->graph_exec || !(key == ctx->graph_key)) {
+        drop_graph(ctx);
+        p.rbuf = ctx->d_rbuf;
+        p.gring = ctx->d_gring;
+        p.ring_rows = s.ring_rows;
+        p.tick_rows = s.tick_rows;
+        p.tiles_per_phase = s.tiles_per_phase;
+        CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        const int D = ctx->D;
+        if (prec == DODE_PREC_BF16 && e == cudaSuccess)
+            e = launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, gs);
+        if (e == cudaSuccess)
+            e = launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, D, ctx->P,
+                                    ctx->N, ctx->Np, ctx->d_pt, gs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), gs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev0, gs);
+        if (e == cudaSuccess) e = launch_fused(p, prec, s.grid, s.block, s.smem, gs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, gs);
+        if (e == cudaSuccess && q_out)
+            e = launch_transpose_out(ctx->d_q, q_out, D, ctx->N, ctx->Np, ctx->K, 1.f, gs);
+        if (e == cudaSuccess && loss_out)
+            e = cudaMemcpyAsync(loss_out, ctx->d_loss, D * sizeof(double), cudaMemcpyDeviceToDevice, gs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(gs, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->graph_exec = nullptr;
+            return fail(ctx, DODE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
+        ctx->graph_key = key;
+    }
+    if (gs != ctx->stream) CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGraphLaunch(ctx->graph_exec, gs));
+    if (gs != ctx->stream) CU(cudaStreamSynchronize(gs));
+    ctx->last_launches = 1;
+    ctx->total_launches += kernels;
+    return DODE_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int dode_set_max_ctas(dode_ctx *ctx, int32_t max_ctas) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (max_ctas < 0) return fail(ctx, DODE_ERR_ARG, "max_ctas >= 0");
+    ctx->opt.max_ctas = max_ctas;
+    return DODE_OK;
+}
 
 void dode_default_options(dode_options *o) {
     if (!o) return;
@@ -459,6 +562,8 @@ void dode_default_options(dode_options *o) {
     o->ctas_per_sm = 0;
     o->device = -1;
     o->stream = nullptr;
+    o->use_graph = 0;
+    o->max_ctas = 0;
 }
 
 const char *dode_last_error(const dode_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -493,7 +598,8 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
         return bail(DODE_ERR_ARG, "route sizes / pointers");
     if (o.n_intervals < 1 || o.interval_s < 1 || o.ticks_per_s < 1 || !std::isfinite(o.theta_per_min) ||
         !(o.eps >= 0.f) || o.row_chunk < 0 || (o.form != DODE_FORM_FUSED && o.form != DODE_FORM_PLAIN) ||
-        (o.precision != DODE_PREC_FP32 && o.precision != DODE_PREC_BF16) || o.block_threads < 0 || o.ctas_per_sm < 0)
+        (o.precision != DODE_PREC_FP32 && o.precision != DODE_PREC_BF16) || o.block_threads < 0 || o.ctas_per_sm < 0 ||
+        o.max_ctas < 0 || (o.use_graph != 0 && o.use_graph != 1))
         return bail(DODE_ERR_ARG, "options");
     const long long ipt = (long long)o.interval_s * o.ticks_per_s;
     if (ipt < 2 || ipt > (1 << 24) || ipt * o.n_intervals > (1LL << 29))
@@ -647,6 +753,7 @@ void dode_destroy(dode_ctx *ctx) {
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
 }
 
@@ -863,6 +970,7 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
                            cudaMemcpyDeviceToDevice, ctx->stream));
     } else {
         if ((size_t)iters * D > ctx->trace_cap) {
+            drop_graph(ctx);
             CU(dalloc(&ctx->d_trace, (size_t)iters * D));
             ctx->trace_cap = (size_t)iters * D;
         }
@@ -871,6 +979,17 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
         p.iters = iters;
         p.eta = step;
         p.trace = iters > 0 ? ctx->d_trace : nullptr;
+        if (ctx->opt.use_graph && ptr_kind == DODE_PTR_DEVICE) {
+            rc = solve_graph(ctx, p, iters, step, q_out, loss_out);
+            if (rc) return rc;
+            ctx->trace_iters = iters;
+            rc = finish_timing(ctx);
+            if (rc) return rc;
+            rc = check_device_error(ctx);
+            if (rc) return rc;
+            CU(cudaStreamSynchronize(ctx->stream));
+            return DODE_OK;
+        }
         if (ctx->opt.precision == DODE_PREC_BF16)
             CUL(launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, ctx->stream));
         rc = run_fused(ctx, p, ctx->opt.precision);

@@ -152,6 +152,7 @@ cudaError_t launch_route_choice(const float *C, const int32_t *rod, const int32_
 cudaError_t launch_fused(const FusedParams &p, int precision, int grid, int block, size_t smem,
                          cudaStream_t s);
 cudaError_t fused_occupancy(int precision, int block, size_t smem, int *blocks_per_sm);
+cudaError_t fused_set_attr(bool smem_ring, bool smem_ticks, int precision, size_t smem);
 cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);

@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
 
         for (int it = 0;; ++it) {
             // ------------------------------ forward sweep ------------------------------
-            float lsum = 0.f;
+            double lsum = 0.0;     // FP64: the loss resolves differences far below one cell's rounding
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
                 const int ntask = nt * p.K;
@@ -530,19 +530,20 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     for (int r0 = 0; r0 < rows; r0 += 32) {
                         const int r = r0 + lane;
                         const int h = pb0 + r;
-                        float x[2], c[2];
+                        double x[2];
+                        float c[2];
                         bool on[2];
 #pragma unroll
                         for (int u = 0; u < 2; ++u) {
                             const int o = o0 + u * nwarps;
-                            x[u] = 0.f;
+                            x[u] = 0.0;
                             c[u] = 0.f;
                             on[u] = false;
                             if (o < p.O && r < rows) {
                                 if (SMEM_RING) {
                                     const int idx = o * s.R + r;
                                     const long long v = ((long long)s.hi[idx] << 32) | (long long)s.lo[idx];
-                                    x[u] = (float)((double)v * kFxInv);
+                                    x[u] = (double)v * kFxInv;
                                 } else {
                                     float *cell = gacc + (size_t)o * p.Np + h;
                                     x[u] = *cell;
@@ -559,11 +560,11 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                             const int o = o0 + u * nwarps;
                             if (o < p.O && r < rows) {
                                 if (p.mode == MODE_FORWARD) {
-                                    p.xout[((size_t)day * p.O + o) * p.Np + h] = x[u];
+                                    p.xout[((size_t)day * p.O + o) * p.Np + h] = (float)x[u];
                                 } else {
-                                    const float rr = on[u] ? x[u] - c[u] : 0.f;
+                                    const double rr = on[u] ? x[u] - (double)c[u] : 0.0;
                                     lsum += rr * rr;
-                                    Operand<PREC>::store_r(rb, (size_t)o * p.Np + h, rr);
+                                    Operand<PREC>::store_r(rb, (size_t)o * p.Np + h, (float)rr);
                                 }
                             }
                         }
@@ -599,7 +600,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 if (threadIdx.x == 0) s_task = 0;
                 __syncthreads();
             }
-            const double loss_day = block_sum((double)lsum, s_red);
+            const double loss_day = block_sum(lsum, s_red);
             if (threadIdx.x == 0) {
                 if (p.mode == MODE_SOLVE && it < p.iters && p.trace) p.trace[(size_t)it * p.n_days + day] = (float)loss_day;
                 if (p.mode != MODE_SOLVE || it == p.iters) p.loss[day] = loss_day;
@@ -643,15 +644,35 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     }
 }
 
+// Raise a variant's dynamic shared-memory limit once to the largest size asked
+// for (so that launches made during a stream capture need no attribute call).
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
+static cudaError_t set_attr_one(size_t smem) {
+    static size_t limit = 48 * 1024;
+    if (smem <= limit) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_fused<PREC, SMEM_RING, SMEM_TICKS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) limit = smem;
+    return e;
+}
+
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
 static cudaError_t launch_one(const FusedParams &p, int grid, int block, size_t smem, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<PREC, SMEM_RING, SMEM_TICKS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = set_attr_one<PREC, SMEM_RING, SMEM_TICKS>(smem);
+    if (e != cudaSuccess) return e;
     k_fused<PREC, SMEM_RING, SMEM_TICKS><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t fused_set_attr(bool smem_ring, bool smem_ticks, int precision, size_t smem) {
+    if (precision == 1) {
+        if (smem_ring && smem_ticks) return set_attr_one<1, true, true>(smem);
+        if (smem_ring) return set_attr_one<1, true, false>(smem);
+        return set_attr_one<1, false, false>(smem);
+    }
+    if (smem_ring && smem_ticks) return set_attr_one<0, true, true>(smem);
+    if (smem_ring) return set_attr_one<0, true, false>(smem);
+    return set_attr_one<0, false, false>(smem);
 }
 
 template <int PREC>

@@ -31,7 +31,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
            "dode_loss_grad", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
-           "dode_last_kernel_ms", "dode_last_launches", "dode_total_launches", "dode_set_launch", "dode_set_stream",
+           "dode_last_kernel_ms", "dode_last_launches", "dode_total_launches", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
 
@@ -57,7 +57,7 @@ class dode_options(ct.Structure):
                 ("theta_per_min", ct.c_float), ("eps", ct.c_float), ("row_chunk", ct.c_int32),
                 ("seed", ct.c_uint64), ("form", ct.c_int32), ("precision", ct.c_int32),
                 ("block_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32), ("device", ct.c_int32),
-                ("stream", ct.c_void_p)]
+                ("stream", ct.c_void_p), ("use_graph", ct.c_int32), ("max_ctas", ct.c_int32)]
 
 
 _lib = None
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "dode_last_launches": (i64, [vp]),
         "dode_total_launches": (i64, [vp]),
         "dode_set_launch": (ct.c_int, [vp, i32, i32]),
+        "dode_set_max_ctas": (ct.c_int, [vp, i32]),
         "dode_set_stream": (ct.c_int, [vp, vp]),
         "dode_last_error": (ct.c_char_p, [vp]),
         "dode_destroy": (None, [vp]),
@@ -310,5 +311,7 @@ class Context:
     def total_launches(self) -> int:
         return int(load().dode_total_launches(self.h))
 
-    def set_launch(self, block_threads: int, ctas_per_sm: int) -> None:
+    def set_launch(self, block_threads: int, ctas_per_sm: int, max_ctas: int = 0) -> None:
         self._check(load().dode_set_launch(self.h, block_threads, ctas_per_sm))
+        self.opt.max_ctas = max_ctas
+        self._check(load().dode_set_max_ctas(self.h, max_ctas))

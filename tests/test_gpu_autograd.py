@@ -45,7 +45,7 @@ def test_autograd_matches_oracle_and_finite_differences():
         dth_tot += dtho
         dabs_tot += dabs
         assert rel_norm(q.grad[d].cpu().numpy(), dqo) < 1e-4
-    assert float(L) == pytest.approx(lo_tot, rel=1e-5)
+    assert float(L.detach()) == pytest.approx(lo_tot, rel=1e-5)
     assert abs(float(theta.grad) - dth_tot) <= 1e-5 * dabs_tot
     # central differences (h = 1e-3) of the GPU loss itself
     h = 1e-3
@@ -54,12 +54,15 @@ def test_autograd_matches_oracle_and_finite_differences():
         lm = float(dode_loss(q, theta - h, ctx))
     fd = (lp - lm) / (2 * h)
     assert float(theta.grad) == pytest.approx(fd, rel=2e-3)
+    # L is quadratic in q, so central differences are exact for any step: a
+    # step of 0.5 vehicles lifts the difference well above FP32 rounding
+    hq = 0.5
     for (d, hh, od) in [(0, 100, 3), (3, 200, 17), (6, 80, 29)]:
         e = torch.zeros_like(q)
         e[d, hh, od] = 1.0
         with torch.no_grad():
-            fdq = (float(dode_loss(q + h * e, theta, ctx)) - float(dode_loss(q - h * e, theta, ctx))) / (2 * h)
-        assert float(q.grad[d, hh, od]) == pytest.approx(fdq, rel=2e-3, abs=0.05)
+            fdq = (float(dode_loss(q + hq * e, theta, ctx)) - float(dode_loss(q - hq * e, theta, ctx))) / (2 * hq)
+        assert float(q.grad[d, hh, od]) == pytest.approx(fdq, rel=2e-3, abs=1e-3)
 
 
 def test_autograd_bf16_form_close_to_fp32():
