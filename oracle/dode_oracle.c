@@ -379,16 +379,42 @@ uint64_t or_splitmix64_next(uint64_t *state) {
     return z ^ (z >> 31);
 }
 
+/* Output number i (0-based) of the SplitMix64 stream that starts at state s: */
+/* every step adds the same constant to the state, so the state i steps on   */
+/* is s + i * gamma and one more step yields output i.                        */
+uint64_t or_splitmix64_at(uint64_t s, uint64_t i) {
+    uint64_t st = s + i * 0x9E3779B97F4A7C15ULL;
+    return or_splitmix64_next(&st);
+}
+
+typedef struct {
+    uint64_t key;
+    int32_t row;
+} or_keyed_row;
+
+static int or_cmp_keyed(const void *a, const void *b) {
+    const or_keyed_row *x = (const or_keyed_row *)a, *y = (const or_keyed_row *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->row > y->row) - (x->row < y->row);
+}
+
 /* permutate(range(n)) of Algorithm 1 over the observed rows of one day and  */
-/* epoch: Fisher-Yates with u = top 53 bits of SplitMix64 / 2^53,           */
-/* state seeded with seed XOR (day << 32 | epoch).                          */
+/* epoch.  Every row id r draws the key = output number r of SplitMix64      */
+/* started at seed ^ (day << 32 | epoch); the rows are put in ascending      */
+/* order of (key, row id).  Ordering i.i.d. uniform keys gives a uniformly   */
+/* random permutation, and a row's key does not depend on which other rows   */
+/* are observed.                                                             */
 void or_permute_rows(int32_t *rows, int32_t n_rows, uint64_t seed, int32_t day, int32_t epoch) {
-    uint64_t st = seed ^ (((uint64_t)(uint32_t)day << 32) | (uint64_t)(uint32_t)epoch);
-    for (int32_t i = n_rows - 1; i >= 1; --i) {
-        double u = (double)(or_splitmix64_next(&st) >> 11) * (1.0 / 9007199254740992.0);
-        int32_t j = (int32_t)(u * (double)(i + 1));
-        int32_t t = rows[i]; rows[i] = rows[j]; rows[j] = t;
+    uint64_t s0 = seed ^ (((uint64_t)(uint32_t)day << 32) | (uint64_t)(uint32_t)epoch);
+    if (n_rows <= 1) return;
+    or_keyed_row *t = (or_keyed_row *)malloc(sizeof(or_keyed_row) * (size_t)n_rows);
+    for (int32_t i = 0; i < n_rows; ++i) {
+        t[i].key = or_splitmix64_at(s0, (uint64_t)(uint32_t)rows[i]);
+        t[i].row = rows[i];
     }
+    qsort(t, (size_t)n_rows, sizeof(or_keyed_row), or_cmp_keyed);
+    for (int32_t i = 0; i < n_rows; ++i) rows[i] = t[i].row;
+    free(t);
 }
 
 /* ------------------------------------------------------------------------ */

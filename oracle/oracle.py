@@ -60,6 +60,8 @@ def lib():
         L.or_loss_grad_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p, _f64p, _f64p, _f64p]
         L.or_splitmix64_next.restype = ct.c_uint64
         L.or_splitmix64_next.argtypes = [ct.POINTER(ct.c_uint64)]
+        L.or_splitmix64_at.restype = ct.c_uint64
+        L.or_splitmix64_at.argtypes = [ct.c_uint64, ct.c_uint64]
         L.or_permute_rows.argtypes = [_i32p, ct.c_int32, ct.c_uint64, ct.c_int32, ct.c_int32]
         L.or_solve_days.restype = ct.c_int
         L.or_solve_days.argtypes = [ct.c_void_p, ct.c_int32, _i32p, _f32p, _f32p, _u8p, ct.c_double,
@@ -262,6 +264,11 @@ class Day:
 def splitmix64(seed: int, n: int) -> list:
     st = ct.c_uint64(seed)
     return [int(lib().or_splitmix64_next(ct.byref(st))) for _ in range(n)]
+
+
+def splitmix64_at(state: int, i: int) -> int:
+    """Output number i of the SplitMix64 stream that starts at ``state``."""
+    return int(lib().or_splitmix64_at(ct.c_uint64(state), ct.c_uint64(i)))
 
 
 def permute_rows(rows: np.ndarray, seed: int, day: int, epoch: int) -> np.ndarray:

@@ -406,7 +406,23 @@ def test_loss_grad_matches_central_differences():
 def test_splitmix64_published_vectors():
     g = _golden("splitmix64.json")
     for s in g["sequences"]:
-        assert orc.splitmix64(s["seed"], len(s["outputs"])) == [int(v) for v in s["outputs"]]
+        outs = [int(v) for v in s["outputs"]]
+        assert orc.splitmix64(s["seed"], len(outs)) == outs
+        # the indexed form (output i straight from the state) agrees with stepping
+        assert [orc.splitmix64_at(s["seed"], i) for i in range(len(outs))] == outs
+
+
+def test_permutation_orders_rows_by_their_stream_outputs():
+    # rows sorted by (output number row of the stream, row), with the outputs
+    # taken by stepping the published generator from seed ^ (day << 32 | epoch)
+    seed, day, epoch = 0xDEADBEEF12345678, 5, 17
+    rows = np.array([3, 4, 9, 10, 11, 20, 21, 39, 40], np.int32)   # an observed subset
+    outs = orc.splitmix64(seed ^ ((day << 32) | epoch), 41)
+    want = sorted(rows.tolist(), key=lambda r: (outs[r], r))
+    assert orc.permute_rows(rows, seed=seed, day=day, epoch=epoch).tolist() == want
+    # a row keeps its key whichever other rows are observed
+    sub = rows[::2]
+    assert orc.permute_rows(sub, seed=seed, day=day, epoch=epoch).tolist() == [r for r in want if r in set(sub.tolist())]
 
 
 def test_permutation_is_uniform():
