@@ -46,10 +46,11 @@ def shard_days(n_days: int, rank: int, world: int) -> list:
     return list(range(rank * n_days, (rank + 1) * n_days))
 
 
-def measured_traffic(workload: str, precision: str):
-    """DRAM bytes per day-iteration of the fused kernel from the committed ncu
-    summary, if it was taken of this workload, this precision and the current
-    kernel source (matched by hash); else None."""
+def measured_traffic(workload: str, precision: str, key: str = "bytes_per_day_iteration"):
+    """Per day-iteration figure ``key`` (DRAM bytes, or warp instructions) of the
+    fused kernel from the committed ncu summary, if it was taken of this
+    workload, this precision and the current kernel source (matched by hash);
+    else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "fused_kernel_corridor-3yr-152d_traffic.txt")
     try:
@@ -65,7 +66,7 @@ def measured_traffic(workload: str, precision: str):
         return None
     if workload != "corridor-3yr" or precision != "bf16" or "BF16" not in rec.get("kernel", ""):
         return None
-    return float(rec["bytes_per_day_iteration"])
+    return float(rec[key]) if key in rec else None
 
 
 def _peaks() -> dict:
@@ -262,7 +263,8 @@ def run_gpu(args):
     days = shard_days(w.n_days, rank, world)
     prec = dode.PREC_BF16 if args.precision == "bf16" else dode.PREC_FP32
     form = dode.FORM_PLAIN if args.form == "plain" else dode.FORM_FUSED
-    ctx = dode.Context.from_workload(w, form=form, precision=prec, use_graph=1 if args.graph else 0)
+    ctx = dode.Context.from_workload(w, form=form, precision=prec, use_graph=1 if args.graph else 0,
+                                     row_chunk=args.row_chunk, day_base=days[0])
     ctx.use_torch_stream()
     sp, counts, mask = gpu_inputs(w, days)
     tuned = None
@@ -356,6 +358,21 @@ def run_gpu(args):
             "peak_source": "measured" if peak else "fallback", "bytes_per_unit": per_unit,
             "kernel_ms": kms}
 
+    # instruction-issue roofline: measured warp instructions per day-iteration x
+    # day-iterations/s of the kernel against 4 issue slots per SM per cycle at the
+    # sampled clock
+    issue = None
+    ipu = measured_traffic(w.name, args.precision, "warp_instructions_per_day_iteration") \
+        if form == dode.FORM_FUSED else None
+    if ipu is not None:
+        mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_issue = n_sm * 4 * mhz * 1e6
+        got = ipu * D * E / (kms / 1e3)
+        issue = {"bound": "issue", "achieved": got, "peak": peak_issue, "unit": "warp-instr/s",
+                 "frac": got / peak_issue, "instr_per_unit": ipu,
+                 "source": "ncu smsp__inst_executed.sum of a 152-day capture of this kernel"}
+
     # comparison forms at equal epochs from q = 0: plain FP32, fused FP32, and this form
     forms = {}
     if args.compare_epochs > 0 and rank == 0:
@@ -402,12 +419,14 @@ def run_gpu(args):
             "config": {"workload": w.name, "days_per_gpu": D, "intervals": N, "od_pairs": K,
                        "routes": w.routes.n_routes, "links": A, "detectors": O, "epochs_per_step": E,
                        "form": args.form, "precision": args.precision, "graph": bool(args.graph),
+                       "row_chunk": args.row_chunk,
                        "launch": tuned or {"block": args.block, "ctas_per_sm": args.ctas},
                        "l2": "inputs larger than L2 (reloaded every step)"},
             "e2e": {"value": e2e_value, "unit": "day-iter/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "issue_roofline": issue,
             "cpu_baseline": cpu,
             "clocks": clk,
             "forms": forms,
@@ -432,6 +451,8 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=500)
     ap.add_argument("--step", type=float, default=5.0)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--row-chunk", type=int, default=0,
+                    help="Algorithm 1's row batch b (0 = all observed rows in each update)")
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--block", type=int, default=0)

@@ -111,6 +111,8 @@ typedef struct {
                                 work (captured on first use, re-captured when iters, step, theta or
                                 the launch shape change) */
     int32_t max_ctas;        /* cap on resident CTAs of the fused kernel (0 = as many as fit) */
+    int32_t day_base;        /* index of the first loaded day in the caller's day numbering (>= 0);
+                                seeds the row permutation of row_chunk > 0 */
 } dode_options;
 
 typedef struct dode_ctx dode_ctx;
@@ -155,9 +157,13 @@ int dode_set_counts(dode_ctx *ctx, const float *counts, const uint8_t *mask, int
  *             queue and runs each day's epochs back to back.
  *   q_out     [D][N][n_od] final OD flows (ptr_kind), may be NULL
  *   loss_out  [D] masked squared loss of the final q, FP64 (ptr_kind), may be NULL
- * One epoch with row_chunk = 0 is one full-row update per day; with
- * row_chunk = b > 0 the observed rows are permuted (SplitMix64 Fisher-Yates,
- * state seed ^ (day << 32 | epoch)) and updated in chunks of b rows.
+ * One epoch with row_chunk = 0 is one full-row update per day.  With
+ * row_chunk = b > 0 (fused form) each epoch permutes the day's observed rows
+ * (Algorithm 1's permutate: row r = h * n_obs + o gets the key SplitMix64
+ * output number r of the stream seeded with seed ^ (day << 32 | epoch), day =
+ * day_base + index in the loaded set; rows go in ascending (key, r)) and
+ * makes one update per run of b consecutive rows (the last run partial);
+ * the loss trace still reports the full masked loss at each epoch start.
  * Errors: DODE_ERR_STATE (no days loaded), DODE_ERR_ARG, DODE_ERR_UNSUPPORTED
  * (row_chunk > 0 with the plain form), DODE_ERR_CUDA.
  */

@@ -60,6 +60,11 @@ struct dode_ctx {
     size_t rbuf_bytes = 0;
     float *d_gring = nullptr;
     size_t gring_bytes = 0;
+    // row-chunk ranking scratch (row_chunk > 0): chunk labels, key-bin counts, straddling-bin lists
+    int32_t *d_lab = nullptr, *d_rc_row = nullptr;
+    uint32_t *d_rc_bins = nullptr;
+    unsigned long long *d_rc_key = nullptr;
+    size_t rc_grid = 0;
     int *d_queue = nullptr, *d_err = nullptr;
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
@@ -104,6 +109,7 @@ int fail(dode_ctx *c, int code, const std::string &msg) {
     do {                                                                                         \
         cudaError_t e_ = (call);                                                                 \
         if (e_ != cudaSuccess) {                                                                 \
+            (void)cudaGetLastError(); /* a non-sticky error must not surface in a later call */  \
             int code_ = (e_ == cudaErrorMemoryAllocation) ? DODE_ERR_OOM : DODE_ERR_CUDA;        \
             return fail(ctx, code_, std::string(#call) + ": " + cudaGetErrorString(e_));         \
         }                                                                                        \
@@ -312,7 +318,28 @@ int ensure_slots(dode_ctx *ctx, const FusedShape &s, int precision) {
         CU(cudaMalloc(&ctx->d_gring, gelems * 4));
         ctx->gring_bytes = gelems * 4;
     }
+    if (ctx->opt.row_chunk > 0 && (size_t)s.grid > ctx->rc_grid) {
+        drop_graph(ctx);
+        const size_t g = (size_t)s.grid, cells = (size_t)ctx->O * ctx->N;
+        CU(dalloc(&ctx->d_lab, g * ctx->O * ctx->Np));
+        CU(dalloc(&ctx->d_rc_bins, g * 3 * kRankBins));
+        CU(dalloc(&ctx->d_rc_key, g * cells));
+        CU(dalloc(&ctx->d_rc_row, g * cells));
+        ctx->rc_grid = g;
+    }
     return DODE_OK;
+}
+
+void slot_params(const dode_ctx *ctx, const FusedShape &s, FusedParams *p) {
+    p->rbuf = ctx->d_rbuf;
+    p->gring = ctx->d_gring;
+    p->ring_rows = s.ring_rows;
+    p->tick_rows = s.tick_rows;
+    p->tiles_per_phase = s.tiles_per_phase;
+    p->lab = ctx->d_lab;
+    p->rc_bins = ctx->d_rc_bins;
+    p->rc_key = ctx->d_rc_key;
+    p->rc_row = ctx->d_rc_row;
 }
 
 FusedParams base_params(dode_ctx *ctx) {
@@ -352,6 +379,9 @@ FusedParams base_params(dode_ctx *ctx) {
     p.theta = ctx->opt.theta_per_min;
     p.queue = ctx->d_queue;
     p.err = ctx->d_err;
+    p.row_chunk = 0;
+    p.seed = ctx->opt.seed;
+    p.day_base = ctx->opt.day_base;
     return p;
 }
 
@@ -361,11 +391,7 @@ int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
     if (rc) return rc;
     rc = ensure_slots(ctx, s, precision);
     if (rc) return rc;
-    p.rbuf = ctx->d_rbuf;
-    p.gring = ctx->d_gring;
-    p.ring_rows = s.ring_rows;
-    p.tick_rows = s.tick_rows;
-    p.tiles_per_phase = s.tiles_per_phase;
+    slot_params(ctx, s, &p);
     CUL(launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, ctx->D, ctx->P, ctx->N,
                             ctx->Np, ctx->d_pt, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
@@ -495,11 +521,7 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
     int64_t kernels = 3 + (prec == DODE_PREC_BF16 ? 1 : 0) + (q_out ? 1 : 0);
     if (!ctx->graph_exec || !(key == ctx->graph_key)) {
         drop_graph(ctx);
-        p.rbuf = ctx->d_rbuf;
-        p.gring = ctx->d_gring;
-        p.ring_rows = s.ring_rows;
-        p.tick_rows = s.tick_rows;
-        p.tiles_per_phase = s.tiles_per_phase;
+        slot_params(ctx, s, &p);
         CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         const int D = ctx->D;
@@ -509,9 +531,11 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
             e = launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, D, ctx->P,
                                     ctx->N, ctx->Np, ctx->d_pt, gs);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), gs);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev0, gs);
+        // external event-record nodes: the events complete with each replay, so
+        // the kernel timer works for graph launches too
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->ev0, gs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_fused(p, prec, s.grid, s.block, s.smem, gs);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev1, gs);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->ev1, gs, cudaEventRecordExternal);
         if (e == cudaSuccess && q_out)
             e = launch_transpose_out(ctx->d_q, q_out, D, ctx->N, ctx->Np, ctx->K, 1.f, gs);
         if (e == cudaSuccess && loss_out)
@@ -522,6 +546,7 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
         if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
+            (void)cudaGetLastError();
             ctx->graph_exec = nullptr;
             return fail(ctx, DODE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
         }
@@ -599,8 +624,10 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     if (o.n_intervals < 1 || o.interval_s < 1 || o.ticks_per_s < 1 || !std::isfinite(o.theta_per_min) ||
         !(o.eps >= 0.f) || o.row_chunk < 0 || (o.form != DODE_FORM_FUSED && o.form != DODE_FORM_PLAIN) ||
         (o.precision != DODE_PREC_FP32 && o.precision != DODE_PREC_BF16) || o.block_threads < 0 || o.ctas_per_sm < 0 ||
-        o.max_ctas < 0 || (o.use_graph != 0 && o.use_graph != 1))
+        o.max_ctas < 0 || (o.use_graph != 0 && o.use_graph != 1) || o.day_base < 0)
         return bail(DODE_ERR_ARG, "options");
+    if (o.row_chunk > 0 && (long long)o.n_intervals * net->n_obs >= (1LL << 31))
+        return bail(DODE_ERR_ARG, "row_chunk > 0 needs n_intervals * n_obs < 2^31 row ids");
     const long long ipt = (long long)o.interval_s * o.ticks_per_s;
     if (ipt < 2 || ipt > (1 << 24) || ipt * o.n_intervals > (1LL << 29))
         return bail(DODE_ERR_ARG, "interval of 2 .. 2^24 ticks and a day of at most 2^29 ticks");
@@ -750,6 +777,10 @@ void dode_destroy(dode_ctx *ctx) {
     dfree(ctx->d_err);
     if (ctx->d_rbuf) cudaFree(ctx->d_rbuf);
     dfree(ctx->d_gring);
+    dfree(ctx->d_lab);
+    dfree(ctx->d_rc_bins);
+    dfree(ctx->d_rc_key);
+    dfree(ctx->d_rc_row);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -939,7 +970,8 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
     if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
     if (iters < 0 || !(step > 0.f) || !std::isfinite(step) || batch < 0 || bad_ptr_kind(ptr_kind))
         return fail(ctx, DODE_ERR_ARG, "solve arguments");
-    if (ctx->opt.row_chunk > 0) return fail(ctx, DODE_ERR_UNSUPPORTED, "row_chunk > 0 is not supported by this build");
+    if (ctx->opt.row_chunk > 0 && ctx->opt.form == DODE_FORM_PLAIN)
+        return fail(ctx, DODE_ERR_UNSUPPORTED, "row_chunk > 0 needs the fused form");
     int rc = set_device(ctx);
     if (rc) return rc;
     const int D = ctx->D;
@@ -976,6 +1008,7 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
         }
         FusedParams p = base_params(ctx);
         p.mode = MODE_SOLVE;
+        p.row_chunk = ctx->opt.row_chunk;
         p.iters = iters;
         p.eta = step;
         p.trace = iters > 0 ? ctx->d_trace : nullptr;

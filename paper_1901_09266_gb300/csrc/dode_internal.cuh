@@ -24,6 +24,7 @@ namespace dode {
 constexpr int kWarp = 32;
 constexpr int kTileW = 31;            // windows per warp task (32 boundaries)
 constexpr int kMaxRouteLinks = 64;
+constexpr int kRankBins = 4096;       // row-chunk ranking: bins on the keys' top 12 bits
 
 enum Mode : int { MODE_SOLVE = 0, MODE_FORWARD = 1, MODE_LOSS = 2, MODE_LOSS_GRAD = 3 };
 
@@ -94,6 +95,14 @@ struct FusedParams {
     int tiles_per_phase;       // F (upper bound; the kernel lowers it for days with long trips)
     int *queue;
     int *err;
+    // row chunks of Algorithm 1 (SOLVE with row_chunk = b > 0)
+    int row_chunk;
+    int day_base;
+    unsigned long long seed;
+    int32_t *lab;              // [grid][O][Np] chunk of each observed cell for the current epoch
+    uint32_t *rc_bins;         // [grid][3][kRankBins] key-bin counts, first ranks, fill cursors
+    unsigned long long *rc_key;  // [grid][O N] keys of the rows in bins that straddle a chunk boundary
+    int32_t *rc_row;           // [grid][O N] their row ids
 };
 
 struct PrepParams {

@@ -89,6 +89,7 @@ struct Shared {
     const int4 *rinfo;    // [P] OD-major: (route, first link, links, 0)
     const int2 *odr;      // [K] route range of each OD in rinfo
     const int *task_od;   // [K] processing order
+    int *carry;           // set once any deposit of this CTA carried into a high word
     int R, RW, pb;
 };
 
@@ -163,14 +164,20 @@ __device__ __forceinline__ void deposit(const Shared &s, float *gacc, int idx, f
     if (FAST || (sv >= 0.f && sv < 4.0e9f)) {
         const uint32_t u = __float2uint_rn(sv);
         const uint32_t old = atomicAdd(&s.lo[idx], u);
-        if (old + u < old) atomicAdd(&s.hi[idx], 1);
+        if (old + u < old) {
+            atomicAdd(&s.hi[idx], 1);
+            *s.carry = 1;
+        }
         return;
     }
     const long long fx = __float2ll_rn(sv);
     const uint32_t u = (uint32_t)fx;
     const uint32_t old = atomicAdd(&s.lo[idx], u);
     const int dh = (int)(fx >> 32) + ((old + u < old) ? 1 : 0);
-    if (dh) atomicAdd(&s.hi[idx], dh);
+    if (dh) {
+        atomicAdd(&s.hi[idx], dh);
+        *s.carry = 1;
+    }
 }
 
 // Cells h0 + 1 .. of a window spanning three or more intervals.  Forward:
@@ -411,6 +418,179 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
     }
 }
 
+// Flush of a phase: rows [pb0, pb0 + rows) of every observed link hold final
+// link flows.  They become masked residuals r = m (xhat - x) (Eq. (nnls)),
+// summed into the loss and written to the CTA's residual slot (or, FORWARD,
+// the flows to xout).  EXACT (forward, loss and gradient calls) converts the
+// 64-bit fixed point to FP64 and sums the loss in FP64.  The solve path
+// (!EXACT) rounds the flow to FP32 once (relative error 6e-8, far below the
+// residual's own scale) and sums r^2 with a compensated FP32 sum per thread,
+// keeping the FP64 pipe out of the loop.  A row chunk (sel >= 0) keeps only
+// the residuals of its rows for the update; the loss still covers all rows.
+// High words are read only once the CTA has seen a carry.
+template <int PREC, bool SMEM_RING, bool EXACT>
+__device__ __forceinline__ void flush_phase(const FusedParams &p, const Shared &s, float *gacc, void *rb,
+                                            const float *cnt, const uint32_t *mk, const int32_t *lab, int sel,
+                                            int day, int pb0, int rows, bool carry, double &lsum, float &ks,
+                                            float &kc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int o0 = warp; o0 < p.O; o0 += 2 * nw) {
+        for (int r0 = 0; r0 < rows; r0 += 32) {
+            const int r = r0 + lane;
+            const int h = pb0 + r;
+            uint32_t lo[2];
+            int hi[2];
+            float xf[2], c[2];
+            bool on[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int o = o0 + u * nw;
+                lo[u] = 0u;
+                hi[u] = 0;
+                xf[u] = 0.f;
+                c[u] = 0.f;
+                on[u] = false;
+                if (o < p.O && r < rows) {
+                    if (SMEM_RING) {
+                        const int idx = o * s.R + r;
+                        lo[u] = s.lo[idx];
+                        if (carry) hi[u] = s.hi[idx];
+                    } else {
+                        float *cell = gacc + (size_t)o * p.Np + h;
+                        xf[u] = *cell;
+                        *cell = 0.f;
+                    }
+                    if (p.mode != MODE_FORWARD) {
+                        on[u] = (mk[(size_t)o * p.Nw + (h >> 5)] >> (h & 31)) & 1u;
+                        c[u] = cnt[(size_t)o * p.Np + h];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int o = o0 + u * nw;
+                if (o < p.O && r < rows) {
+                    const size_t ri = (size_t)o * p.Np + h;
+                    if (EXACT) {
+                        const double x =
+                            SMEM_RING ? (double)(((long long)hi[u] << 32) | (long long)lo[u]) * kFxInv : (double)xf[u];
+                        if (p.mode == MODE_FORWARD) {
+                            p.xout[(size_t)day * p.O * p.Np + ri] = (float)x;
+                        } else {
+                            const double rr = on[u] ? x - (double)c[u] : 0.0;
+                            lsum += rr * rr;
+                            Operand<PREC>::store_r(rb, ri, (float)rr);
+                        }
+                    } else {
+                        const float x =
+                            SMEM_RING ? fmaf((float)hi[u], 4096.f, __uint2float_rn(lo[u]) * 9.5367431640625e-7f)
+                                      : xf[u];
+                        const float rr = on[u] ? x - c[u] : 0.f;
+                        const float y = rr * rr - kc;     // compensated (Kahan) sum
+                        const float t = ks + y;
+                        kc = (t - ks) - y;
+                        ks = t;
+                        const bool use = sel < 0 || (on[u] && lab[ri] == sel);
+                        Operand<PREC>::store_r(rb, ri, use ? rr : 0.f);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// SplitMix64 (Steele, Lea and Flood, 2014) output number i of the stream that
+// starts at state s: each step adds the golden-ratio constant to the state and
+// mixes it, so output i is the mix of s + (i + 1) gamma.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long s, unsigned long long i) {
+    unsigned long long z = s + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Row chunks of Algorithm 1 for one (day, epoch): the epoch visits the day's
+// observed rows in ascending (key, row) order, row r = h O + o drawing key =
+// output r of SplitMix64 seeded with seed ^ (day << 32 | epoch), and updates on
+// runs of b rows.  Each observed cell gets lab = rank / b.  Ranks come from a
+// histogram on the keys' top 12 bits: a bin whose rank range lies in one chunk
+// labels its rows directly; the rows of a bin that straddles a chunk boundary
+// are listed and ranked exactly inside the bin.  Returns the number of chunks.
+__device__ int row_labels(const FusedParams &p, const uint32_t *mk, int gday, int epoch, int *s_n) {
+    uint32_t *cnt = p.rc_bins + (size_t)blockIdx.x * 3 * kRankBins;
+    uint32_t *first = cnt + kRankBins, *cur = first + kRankBins;
+    const size_t cells = (size_t)p.O * p.N;
+    unsigned long long *lkey = p.rc_key + (size_t)blockIdx.x * cells;
+    int32_t *lrow = p.rc_row + (size_t)blockIdx.x * cells;
+    int32_t *lab = p.lab + (size_t)blockIdx.x * p.O * p.Np;
+    const unsigned long long s0 =
+        p.seed ^ (((unsigned long long)(uint32_t)gday << 32) | (unsigned long long)(uint32_t)epoch);
+    const uint32_t b = (uint32_t)p.row_chunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < kRankBins; i += blockDim.x) {
+        cnt[i] = 0u;
+        cur[i] = 0u;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < (int)cells; c += blockDim.x) {    // O N < 2^31 (checked at create)
+        const int o = c / p.N, h = c - o * p.N;
+        if ((mk[(size_t)o * p.Nw + (h >> 5)] >> (h & 31)) & 1u) {
+            const unsigned long long key = splitmix64_at(s0, (unsigned long long)h * p.O + o);
+            atomicAdd(&cnt[key >> 52], 1u);
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {       // exclusive scan of the bin counts: lane l owns 128 consecutive bins
+        constexpr int per = kRankBins / 32;
+        uint32_t sum = 0;
+        for (int i = 0; i < per; ++i) sum += cnt[lane * per + i];
+        uint32_t incl = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        uint32_t run = incl - sum;
+        for (int i = 0; i < per; ++i) {
+            first[lane * per + i] = run;
+            run += cnt[lane * per + i];
+        }
+        if (lane == 31) *s_n = (int)incl;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < (int)cells; c += blockDim.x) {    // O N < 2^31 (checked at create)
+        const int o = c / p.N, h = c - o * p.N;
+        if ((mk[(size_t)o * p.Nw + (h >> 5)] >> (h & 31)) & 1u) {
+            const unsigned long long key = splitmix64_at(s0, (unsigned long long)h * p.O + o);
+            const int bin = (int)(key >> 52);
+            const uint32_t f = first[bin], n = cnt[bin];
+            if (f / b == (f + n - 1) / b) {
+                lab[(size_t)o * p.Np + h] = (int32_t)(f / b);
+            } else {
+                const uint32_t pos = f + atomicAdd(&cur[bin], 1u);
+                lkey[pos] = key;
+                lrow[pos] = h * p.O + o;
+            }
+        }
+    }
+    __syncthreads();
+    for (int bin = warp; bin < kRankBins; bin += nw) {
+        const uint32_t f = first[bin], n = cnt[bin];
+        if (n == 0 || f / b == (f + n - 1) / b) continue;
+        for (uint32_t i = lane; i < n; i += 32) {
+            const unsigned long long ki = lkey[f + i];
+            const int32_t ri = lrow[f + i];
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < n; ++j) {
+                const unsigned long long kj = lkey[f + j];
+                rank += (kj < ki || (kj == ki && lrow[f + j] < ri)) ? 1u : 0u;
+            }
+            lab[(size_t)(ri % p.O) * p.Np + ri / p.O] = (int32_t)((f + rank) / b);
+        }
+    }
+    __syncthreads();
+    return (int)((*s_n + b - 1) / b);
+}
+
 // Dynamic shared memory layout (16-byte aligned blocks):
 //   rinfo int4[P] | odr int2[K] | task_od int[K] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
@@ -442,6 +622,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     __shared__ int s_task;
     __shared__ double s_red[32];
     __shared__ double s_dth;
+    __shared__ int s_nrows;
+    __shared__ int s_carry;
+    s.carry = &s_carry;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nthr = blockDim.x;
@@ -468,7 +651,11 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     } else {
         for (size_t i = threadIdx.x; i < (size_t)p.O * p.Np; i += nthr) gacc[i] = 0.f;
     }
-    if (threadIdx.x == 0) s_task = 0;
+    if (threadIdx.x == 0) {
+        s_task = 0;
+        s_carry = 0;
+    }
+    const bool exact = p.mode != MODE_SOLVE;
 
     while (true) {
         __syncthreads();
@@ -498,9 +685,18 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         if (threadIdx.x == 0) s_dth = 0.0;
         __syncthreads();
 
-        for (int it = 0;; ++it) {
+        // One pass = forward sweep (+ adjoint sweep and step).  Full-row updates
+        // make one pass per epoch; row chunks make one per chunk, the first of
+        // an epoch also giving the epoch's full masked loss.
+        const bool chunked = p.mode == MODE_SOLVE && p.row_chunk > 0;
+        const int32_t *lab = chunked ? p.lab + (size_t)blockIdx.x * p.O * p.Np : nullptr;
+        int nch = 1;
+        for (int it = 0, chunk = 0;;) {
+            if (chunked && it < p.iters && chunk == 0) nch = row_labels(p, mk, p.day_base + day, it, &s_nrows);
+            const int sel = (chunked && it < p.iters) ? chunk : -1;     // chunk of rows in this update
             // ------------------------------ forward sweep ------------------------------
-            double lsum = 0.0;     // FP64: the loss resolves differences far below one cell's rounding
+            double lsum = 0.0;     // EXACT calls: FP64 (finite differences of the loss resolve tiny changes)
+            float ks = 0.f, kc = 0.f;  // solve: compensated FP32 sum
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
                 const int ntask = nt * p.K;
@@ -526,50 +722,13 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 // the spill rows move to the front for the next phase
                 const int span = nt * kTileW;
                 const int rows = min(span, p.N - pb0);
-                for (int o0 = warp; o0 < p.O; o0 += 2 * nwarps) {
-                    for (int r0 = 0; r0 < rows; r0 += 32) {
-                        const int r = r0 + lane;
-                        const int h = pb0 + r;
-                        double x[2];
-                        float c[2];
-                        bool on[2];
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int o = o0 + u * nwarps;
-                            x[u] = 0.0;
-                            c[u] = 0.f;
-                            on[u] = false;
-                            if (o < p.O && r < rows) {
-                                if (SMEM_RING) {
-                                    const int idx = o * s.R + r;
-                                    const long long v = ((long long)s.hi[idx] << 32) | (long long)s.lo[idx];
-                                    x[u] = (double)v * kFxInv;
-                                } else {
-                                    float *cell = gacc + (size_t)o * p.Np + h;
-                                    x[u] = *cell;
-                                    *cell = 0.f;
-                                }
-                                if (p.mode != MODE_FORWARD) {
-                                    on[u] = (mk[(size_t)o * p.Nw + (h >> 5)] >> (h & 31)) & 1u;
-                                    c[u] = cnt[(size_t)o * p.Np + h];
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int o = o0 + u * nwarps;
-                            if (o < p.O && r < rows) {
-                                if (p.mode == MODE_FORWARD) {
-                                    p.xout[((size_t)day * p.O + o) * p.Np + h] = (float)x[u];
-                                } else {
-                                    const double rr = on[u] ? x[u] - (double)c[u] : 0.0;
-                                    lsum += rr * rr;
-                                    Operand<PREC>::store_r(rb, (size_t)o * p.Np + h, (float)rr);
-                                }
-                            }
-                        }
-                    }
-                }
+                const bool carry = s_carry != 0;
+                if (exact)
+                    flush_phase<PREC, SMEM_RING, true>(p, s, gacc, rb, cnt, mk, lab, sel, day, pb0, rows, carry, lsum,
+                                                       ks, kc);
+                else
+                    flush_phase<PREC, SMEM_RING, false>(p, s, gacc, rb, cnt, mk, lab, sel, day, pb0, rows, carry,
+                                                        lsum, ks, kc);
                 if (SMEM_RING) {
                     // move the spill rows [span, span + spill) to the front, zero the rest
                     __syncthreads();
@@ -582,30 +741,34 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                             int vh = 0;
                             if (r < spill) {
                                 vl = lrow[span + r];
-                                vh = hrow[span + r];
+                                if (carry) vh = hrow[span + r];
                             }
                             __syncwarp();
                             if (r < spill) {
                                 lrow[r] = vl;
-                                hrow[r] = vh;
+                                if (carry) hrow[r] = vh;
                             }
                             __syncwarp();
                         }
                         for (int r = spill + lane; r < span + spill; r += 32) {
                             lrow[r] = 0u;
-                            hrow[r] = 0;
+                            if (carry) hrow[r] = 0;
                         }
                     }
                 }
                 if (threadIdx.x == 0) s_task = 0;
                 __syncthreads();
             }
-            const double loss_day = block_sum(lsum, s_red);
-            if (threadIdx.x == 0) {
+            const double loss_day = block_sum(exact ? lsum : (double)ks - (double)kc, s_red);
+            if (threadIdx.x == 0 && chunk == 0) {
                 if (p.mode == MODE_SOLVE && it < p.iters && p.trace) p.trace[(size_t)it * p.n_days + day] = (float)loss_day;
                 if (p.mode != MODE_SOLVE || it == p.iters) p.loss[day] = loss_day;
             }
             if (p.mode == MODE_FORWARD || p.mode == MODE_LOSS || (p.mode == MODE_SOLVE && it >= p.iters)) break;
+            if (chunked && nch == 0) {      // no observed row: the epoch makes no update
+                ++it;
+                continue;
+            }
 
             // ------------------------------ adjoint sweep ------------------------------
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
@@ -640,6 +803,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 if (threadIdx.x == 0) p.dtheta[day] = s_dth;
                 break;
             }
+            if (chunked && ++chunk < nch) continue;
+            chunk = 0;
+            ++it;
         }
     }
 }

@@ -57,7 +57,8 @@ class dode_options(ct.Structure):
                 ("theta_per_min", ct.c_float), ("eps", ct.c_float), ("row_chunk", ct.c_int32),
                 ("seed", ct.c_uint64), ("form", ct.c_int32), ("precision", ct.c_int32),
                 ("block_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32), ("device", ct.c_int32),
-                ("stream", ct.c_void_p), ("use_graph", ct.c_int32), ("max_ctas", ct.c_int32)]
+                ("stream", ct.c_void_p), ("use_graph", ct.c_int32), ("max_ctas", ct.c_int32),
+                ("day_base", ct.c_int32)]
 
 
 _lib = None

@@ -285,7 +285,7 @@ def test_errors_are_reported(c1):
     with pytest.raises(dode.DodeError) as e:
         ctx.solve(1, -1.0)
     assert e.value.code == dode.ERR_ARG
-    ctx2 = dode.Context.from_workload(w, row_chunk=8192)
+    ctx2 = dode.Context.from_workload(w, row_chunk=8192, form=dode.FORM_PLAIN)
     ctx2.set_days(counts, sp, mask)
     with pytest.raises(dode.DodeError) as e:
         ctx2.solve(1, 5.0)

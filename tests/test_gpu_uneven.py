@@ -53,8 +53,8 @@ def test_launch_shapes_and_graph_give_identical_results(uneven):
         res.append(ctx.solve(8, 5.0))
     for q, l in res[1:]:
         np.testing.assert_array_equal(q, res[0][0])
-        # the FP64 per-day loss reduction groups its terms by CTA size
-        np.testing.assert_allclose(l, res[0][1], rtol=1e-13)
+        # the solve's per-thread compensated FP32 loss sums split the cells by CTA size
+        np.testing.assert_allclose(l, res[0][1], rtol=1e-7)
     g = dode.Context.from_workload(w, use_graph=1)
     g.use_torch_stream()
     g.set_days(counts, sp, mask)
