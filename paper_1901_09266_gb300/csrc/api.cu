@@ -31,6 +31,15 @@ struct dode_ctx {
     std::vector<int32_t> pair_k, pair_j, pair_o, rpp;  // observed (route, position) pairs
     std::vector<int2> rpack;                           // (link, observed column) per route position
     int2 *d_rpack = nullptr;
+    // walk groups of the fused kernel (routes from one origin, lexicographic order)
+    std::vector<int4> groute;                          // [P] (route, first position, links, start depth)
+    std::vector<int32_t> gptr, task_grp, rev;          // [G+1], [G], [L]
+    std::vector<int32_t> god_ptr, god, godr_ptr, godr;  // ODs owned by each group and their routes
+    std::vector<int32_t> step_ods;                     // ODs of groups that do not own them
+    int G = 0;
+    int4 *d_groute = nullptr;
+    int32_t *d_gptr = nullptr, *d_task_grp = nullptr, *d_rev = nullptr;
+    int32_t *d_god_ptr = nullptr, *d_god = nullptr, *d_godr_ptr = nullptr, *d_godr = nullptr, *d_step_ods = nullptr;
     float *d_pt = nullptr;                             // route choice table [D][P][Np]
     int32_t *d_rptr = nullptr, *d_rlinks = nullptr, *d_rod = nullptr, *d_obs_col = nullptr, *d_od_ptr = nullptr,
             *d_od_routes = nullptr, *d_task_od = nullptr;
@@ -65,6 +74,8 @@ struct dode_ctx {
     uint32_t *d_rc_bins = nullptr;
     unsigned long long *d_rc_key = nullptr;
     size_t rc_grid = 0;
+    float *d_gp = nullptr;                             // [grid][P][Np] route-level adjoint sums
+    size_t gp_bytes = 0;
     int *d_queue = nullptr, *d_err = nullptr;
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
@@ -246,7 +257,7 @@ struct FusedShape {
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 size_t fused_smem_bytes(const dode_ctx *ctx, int R, int RW) {
-    size_t off = align16((size_t)ctx->P * 16) + align16((size_t)ctx->K * 8) + align16((size_t)ctx->K * 4) +
+    size_t off = align16((size_t)ctx->P * 16) + align16((size_t)(ctx->G + 1) * 4) + align16((size_t)ctx->G * 4) +
                  align16((size_t)ctx->Ow * 4);
     if (R > 0) off = align16(off + (size_t)ctx->O * R * 4);
     if (RW > 0) off += (size_t)ctx->A * RW * 2;
@@ -318,6 +329,14 @@ int ensure_slots(dode_ctx *ctx, const FusedShape &s, int precision) {
         CU(cudaMalloc(&ctx->d_gring, gelems * 4));
         ctx->gring_bytes = gelems * 4;
     }
+    const size_t gpb = (size_t)s.grid * ctx->P * ctx->Np * sizeof(float);
+    if (gpb > ctx->gp_bytes) {
+        drop_graph(ctx);
+        dfree(ctx->d_gp);
+        ctx->gp_bytes = 0;
+        CU(cudaMalloc(&ctx->d_gp, gpb));
+        ctx->gp_bytes = gpb;
+    }
     if (ctx->opt.row_chunk > 0 && (size_t)s.grid > ctx->rc_grid) {
         drop_graph(ctx);
         const size_t g = (size_t)s.grid, cells = (size_t)ctx->O * ctx->N;
@@ -336,10 +355,124 @@ void slot_params(const dode_ctx *ctx, const FusedShape &s, FusedParams *p) {
     p->ring_rows = s.ring_rows;
     p->tick_rows = s.tick_rows;
     p->tiles_per_phase = s.tiles_per_phase;
+    p->gp = ctx->d_gp;
     p->lab = ctx->d_lab;
     p->rc_bins = ctx->d_rc_bins;
     p->rc_key = ctx->d_rc_key;
     p->rc_row = ctx->d_rc_row;
+}
+
+// Walk groups of the fused kernel.  Every route leaving the same origin node
+// starts at the same departure boundaries, so two such routes have identical
+// trajectories over their common link prefix, and each window of that prefix
+// carries the summed flow of the routes through it (forward) and is gathered
+// once for all of them (adjoint).  Routes from one origin are put in
+// lexicographic order of their link sequences -- a depth-first order of their
+// prefix tree -- and cut into groups of at most kGroupRoutes.  In a group,
+// route i is walked from its start depth s_i (its common prefix with route
+// i - 1) to its end; per position j it records E (the last route of the group
+// that shares the prefix up to and including link j, so the window's flow is
+// routes i..E) and a save bit: a later route starts at depth j + 1 from this
+// walk, which stores the entry time (and adjoint partial sum) there.
+void build_groups(dode_ctx *ctx, const int32_t *link_tail) {
+    const int P = ctx->P;
+    auto links_of = [&](int k) {
+        return std::vector<int32_t>(ctx->rlinks.begin() + ctx->rptr[k], ctx->rlinks.begin() + ctx->rptr[k + 1]);
+    };
+    std::vector<int> order(P);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<std::vector<int32_t>> seq(P);
+    for (int k = 0; k < P; ++k) seq[k] = links_of(k);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const int oa = link_tail[seq[a][0]], ob = link_tail[seq[b][0]];
+        if (oa != ob) return oa < ob;
+        return seq[a] < seq[b];
+    });
+    auto lcp = [&](int a, int b) {
+        const size_t n = std::min(seq[a].size(), seq[b].size());
+        size_t i = 0;
+        while (i < n && seq[a][i] == seq[b][i]) ++i;
+        return (int)i;
+    };
+    ctx->groute.assign(P, make_int4(0, 0, 0, 0));
+    ctx->rev.assign(ctx->L, 0);
+    ctx->gptr.assign(1, 0);
+    std::vector<long long> work;
+    int i = 0;
+    while (i < P) {
+        // one origin's routes, cut into groups of at most kGroupRoutes
+        int j = i;
+        const int origin = link_tail[seq[order[i]][0]];
+        while (j < P && link_tail[seq[order[j]][0]] == origin) ++j;
+        for (int g0 = i; g0 < j; g0 += kGroupRoutes) {
+            const int g1 = std::min(j, g0 + kGroupRoutes), m = g1 - g0;
+            std::vector<int> r(order.begin() + g0, order.begin() + g1), st(m, 0);
+            long long w = 0;
+            for (int t = 0; t < m; ++t) {
+                const int k = r[t];
+                st[t] = t == 0 ? 0 : lcp(r[t - 1], k);
+                const int beta = (int)seq[k].size();
+                ctx->groute[g0 + t] = make_int4(k, ctx->rptr[k], beta, st[t]);
+                w += beta - st[t];
+                for (int d = st[t]; d < beta; ++d) {
+                    int e = t;
+                    while (e + 1 < m && lcp(k, r[e + 1]) >= d + 1) ++e;
+                    ctx->rev[ctx->rptr[k] + d] = e << 1;
+                }
+            }
+            // the walk that stores the state a later route starts from: the last
+            // earlier route that passed depth s_e - 1
+            for (int e = 1; e < m; ++e) {
+                if (st[e] == 0) continue;
+                int t = e - 1;
+                while (st[t] > st[e] - 1) --t;
+                ctx->rev[ctx->rptr[r[t]] + st[e] - 1] |= 1;
+            }
+            ctx->gptr.push_back(g1);
+            work.push_back(w);
+        }
+        i = j;
+    }
+    ctx->G = (int)work.size();
+    // a group owns an OD when it holds all of the OD's routes (always, unless an
+    // origin has more than kGroupRoutes routes): its adjoint task then forms g
+    // and takes the step itself; other ODs go through the step pass
+    std::vector<int> gof(P);
+    for (int g = 0; g < ctx->G; ++g)
+        for (int x = ctx->gptr[g]; x < ctx->gptr[g + 1]; ++x) gof[ctx->groute[x].x] = g;
+    std::vector<int> owner(ctx->K, -1);
+    for (int od = 0; od < ctx->K; ++od) {
+        int g0 = -1;
+        bool one = true;
+        for (int r = ctx->od_ptr[od]; r < ctx->od_ptr[od + 1]; ++r) {
+            const int g = gof[ctx->od_routes[r]];
+            if (g0 < 0) g0 = g;
+            else if (g != g0) one = false;
+        }
+        owner[od] = one ? g0 : -1;
+        if (!one) ctx->step_ods.push_back(od);
+    }
+    for (int x = 0; x < P; ++x)        // bit 8 of the start-depth word: the group owns the route's OD
+        if (owner[ctx->rod[ctx->groute[x].x]] == gof[ctx->groute[x].x]) ctx->groute[x].w |= 1 << 8;
+    ctx->god_ptr.assign(1, 0);
+    ctx->godr_ptr.assign(1, 0);
+    for (int g = 0; g < ctx->G; ++g) {
+        std::vector<int> ods;
+        for (int x = ctx->gptr[g]; x < ctx->gptr[g + 1]; ++x) {
+            const int od = ctx->rod[ctx->groute[x].x];
+            if (owner[od] == g && std::find(ods.begin(), ods.end(), od) == ods.end()) ods.push_back(od);
+        }
+        for (int od : ods) {
+            ctx->god.push_back(od);
+            for (int x = ctx->gptr[g]; x < ctx->gptr[g + 1]; ++x)
+                if (ctx->rod[ctx->groute[x].x] == od) ctx->godr.push_back(x - ctx->gptr[g]);
+            ctx->godr_ptr.push_back((int32_t)ctx->godr.size());
+        }
+        ctx->god_ptr.push_back((int32_t)ctx->god.size());
+    }
+    ctx->task_grp.resize(ctx->G);
+    std::iota(ctx->task_grp.begin(), ctx->task_grp.end(), 0);
+    std::stable_sort(ctx->task_grp.begin(), ctx->task_grp.end(), [&](int a, int b) { return work[a] > work[b]; });
 }
 
 FusedParams base_params(dode_ctx *ctx) {
@@ -360,6 +493,18 @@ FusedParams base_params(dode_ctx *ctx) {
     p.od_routes = ctx->d_od_routes;
     p.task_od = ctx->d_task_od;
     p.rpack = ctx->d_rpack;
+    p.groute = ctx->d_groute;
+    p.gptr = ctx->d_gptr;
+    p.task_grp = ctx->d_task_grp;
+    p.rev = ctx->d_rev;
+    p.rod = ctx->d_rod;
+    p.n_groups = ctx->G;
+    p.god_ptr = ctx->d_god_ptr;
+    p.god = ctx->d_god;
+    p.godr_ptr = ctx->d_godr_ptr;
+    p.godr = ctx->d_godr;
+    p.step_ods = ctx->d_step_ods;
+    p.n_step_ods = (int)ctx->step_ods.size();
     p.pt = ctx->d_pt;
     p.ticks = ctx->d_ticks;
     p.counts = ctx->d_counts;
@@ -703,6 +848,7 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     std::stable_sort(ctx->task_od.begin(), ctx->task_od.end(), [&](int a, int b) { return work[a] > work[b]; });
     ctx->rpack.resize(ctx->L);
     for (int j = 0; j < ctx->L; ++j) ctx->rpack[j] = make_int2(ctx->rlinks[j], obs_col[ctx->rlinks[j]]);
+    build_groups(ctx, net->link_tail);
     // observed (route, position) pairs for the plain form
     ctx->rpp.assign(P + 1, 0);
     for (int k = 0; k < P; ++k) {
@@ -743,6 +889,15 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     CUB(upload(&ctx->d_rpp, ctx->rpp, ctx->stream));
     CUB(upload(&ctx->d_len, ctx->len, ctx->stream));
     CUB(upload(&ctx->d_rpack, ctx->rpack, ctx->stream));
+    CUB(upload(&ctx->d_groute, ctx->groute, ctx->stream));
+    CUB(upload(&ctx->d_gptr, ctx->gptr, ctx->stream));
+    CUB(upload(&ctx->d_task_grp, ctx->task_grp, ctx->stream));
+    CUB(upload(&ctx->d_rev, ctx->rev, ctx->stream));
+    CUB(upload(&ctx->d_god_ptr, ctx->god_ptr, ctx->stream));
+    CUB(upload(&ctx->d_god, ctx->god, ctx->stream));
+    CUB(upload(&ctx->d_godr_ptr, ctx->godr_ptr, ctx->stream));
+    CUB(upload(&ctx->d_godr, ctx->godr, ctx->stream));
+    CUB(upload(&ctx->d_step_ods, ctx->step_ods, ctx->stream));
     CUB(cudaMalloc(&ctx->d_queue, sizeof(int)));
     CUB(cudaMalloc(&ctx->d_err, 4 * sizeof(int)));
     CUB(cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));
@@ -773,10 +928,20 @@ void dode_destroy(dode_ctx *ctx) {
     dfree(ctx->d_rpp);
     dfree(ctx->d_len);
     dfree(ctx->d_rpack);
+    dfree(ctx->d_groute);
+    dfree(ctx->d_gptr);
+    dfree(ctx->d_task_grp);
+    dfree(ctx->d_rev);
+    dfree(ctx->d_god_ptr);
+    dfree(ctx->d_god);
+    dfree(ctx->d_godr_ptr);
+    dfree(ctx->d_godr);
+    dfree(ctx->d_step_ods);
     dfree(ctx->d_queue);
     dfree(ctx->d_err);
     if (ctx->d_rbuf) cudaFree(ctx->d_rbuf);
     dfree(ctx->d_gring);
+    dfree(ctx->d_gp);
     dfree(ctx->d_lab);
     dfree(ctx->d_rc_bins);
     dfree(ctx->d_rc_key);

@@ -24,6 +24,7 @@ namespace dode {
 constexpr int kWarp = 32;
 constexpr int kTileW = 31;            // windows per warp task (32 boundaries)
 constexpr int kMaxRouteLinks = 64;
+constexpr int kGroupRoutes = 32;      // routes per walk group of the fused kernel
 constexpr int kRankBins = 4096;       // row-chunk ranking: bins on the keys' top 12 bits
 
 enum Mode : int { MODE_SOLVE = 0, MODE_FORWARD = 1, MODE_LOSS = 2, MODE_LOSS_GRAD = 3 };
@@ -65,6 +66,18 @@ struct FusedParams {
     const int32_t *od_routes;  // [P] routes grouped by OD
     const int32_t *task_od;    // [K] OD processing order (largest work first)
     const int2 *rpack;         // [L] (link, observed column or -1) of every route position
+    const int4 *groute;        // [P] walk order: (route, first position, links, start depth)
+    const int32_t *gptr;       // [G+1] routes of each walk group in groute
+    const int32_t *task_grp;   // [G] group processing order (largest walk first)
+    const int32_t *rev;        // [L] (E << 1) | save of every route position (see build_groups)
+    const int32_t *rod;        // [P] OD pair of each route
+    int n_groups;
+    const int32_t *god_ptr;    // [G+1] ODs owned by each group (all their routes are in it)
+    const int32_t *god;        // owned ODs
+    const int32_t *godr_ptr;   // routes of each owned OD in godr
+    const int32_t *godr;       // their indices in the group's walk order
+    const int32_t *step_ods;   // [n_step_ods] ODs whose routes span groups: step pass
+    int n_step_ods;
     const float *pt;           // [D][P][Np] route choice for the call's theta
     // per-day inputs
     const int32_t *ticks;
@@ -81,6 +94,7 @@ struct FusedParams {
     __nv_bfloat16 *qb;         // [D][K][Np] BF16 operand copy (BF16 form)
     void *rbuf;                // [grid][O][Np] residual slots (f32 or bf16)
     float *gring;              // [grid][O][Np] accumulators when the ring lives in global memory
+    float *gp;                 // [grid][P][Np] route-level adjoint sums of the current phase
     // outputs
     double *loss;              // [D]
     float *trace;              // [iters][D] or null

@@ -86,29 +86,31 @@ struct Shared {
     int *hi;              // [O][R] in global memory: accumulator high words (forward)
     uint16_t *tw;         // [A][RW]: tick window (row = h - pb)
     const uint32_t *colact;
-    const int4 *rinfo;    // [P] OD-major: (route, first link, links, 0)
-    const int2 *odr;      // [K] route range of each OD in rinfo
-    const int *task_od;   // [K] processing order
+    const int4 *groute;   // [P] walk order: (route, first position, links, start depth)
+    const int *gptr;      // [G+1] routes of each walk group
+    const int *task_grp;  // [G] processing order
     int *carry;           // set once any deposit of this CTA carried into a high word
     int R, RW, pb;
 };
 
-// Route links in registers: lane j holds, for link j (and j + 32) of the route,
-// the offset of its tick row and of its accumulator row (kInactive when the
-// link is unobserved or has no observation this day), both relative to pb.
+// Route links in registers: lane j holds, for position j (and j + 32) of the
+// route, the offset of its tick row and of its accumulator row (kInactive when
+// the link is unobserved or has no observation this day), both relative to pb,
+// and the position's walk-group event word (E << 1 | save).
 struct RouteRegs {
-    int t0, o0, t1, o1;
+    int t0, o0, e0, t1, o1, e1;
 };
 
 template <bool SMEM_RING, bool SMEM_TICKS>
 __device__ __forceinline__ RouteRegs load_route(const FusedParams &p, const Shared &s, int l0, int beta) {
     const int lane = threadIdx.x & 31;
-    RouteRegs r{0, kInactive, 0, kInactive};
+    RouteRegs r{0, kInactive, 0, 0, kInactive, 0};
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int j = lane + 32 * half;
         if (j < beta && (half == 0 || beta > 32)) {
             const int2 ao = __ldg(&p.rpack[l0 + j]);
+            const int ev = __ldg(&p.rev[l0 + j]);
             const int a = ao.x, o = ao.y;
             const int tb = SMEM_TICKS ? a * s.RW - s.pb : a * p.Np;
             int ob = kInactive;
@@ -116,24 +118,15 @@ __device__ __forceinline__ RouteRegs load_route(const FusedParams &p, const Shar
             if (half == 0) {
                 r.t0 = tb;
                 r.o0 = ob;
+                r.e0 = ev;
             } else {
                 r.t1 = tb;
                 r.o1 = ob;
+                r.e1 = ev;
             }
         }
     }
     return r;
-}
-
-// Route choice of Eq. (logit) at the lane's departure interval from the route
-// times (differentiable form): shift m and reciprocal normaliser.
-__device__ __forceinline__ void logit_norm(const FusedParams &p, const Shared &s, const float *Cday, int r0, int r1,
-                                           int bi, float &m, float &rden) {
-    m = -INFINITY;
-    for (int i = r0; i < r1; ++i) m = fmaxf(m, -p.theta * Cday[(size_t)s.rinfo[i].x * p.Np + bi]);
-    float den = 0.f;
-    for (int i = r0; i < r1; ++i) den += expf(-p.theta * Cday[(size_t)s.rinfo[i].x * p.Np + bi] - m);
-    rden = 1.f / den;
 }
 
 // Shares of a window [T, hi) of width w over the arrival intervals (Eq. (dar)).
@@ -206,6 +199,42 @@ __device__ __noinline__ float window_tail(const Shared &s, float *gacc, const vo
     return acc;
 }
 
+// Add u units of 2^-20 vehicles (u < 2^32) to cell idx.
+template <bool SMEM_RING>
+__device__ __forceinline__ void deposit_u(const Shared &s, float *gacc, int idx, uint32_t u) {
+    if (!SMEM_RING) {
+        atomicAdd(gacc + idx, (float)((double)u * kFxInv));
+        return;
+    }
+    const uint32_t old = atomicAdd(&s.lo[idx], u);
+    if (old + u < old) {
+        atomicAdd(&s.hi[idx], 1);
+        *s.carry = 1;
+    }
+}
+
+// Integer form of window_tail: cells h0 + 1 .. of a window spanning three or
+// more intervals get rn(W share) each, the window's last cell the remainder
+// of W; cells past the end of the day are dropped.
+template <int PREC, bool SMEM_RING>
+__device__ __noinline__ void window_tail_u(const Shared &s, float *gacc, int idx, int hi, int e, int h, int N,
+                                           int ipt, float inv, float Wf, uint32_t rem) {
+    while (hi > e && h < N) {
+        const int end = min(hi, e + ipt);
+        uint32_t u = rem;
+        if (end < hi) {
+            float share = (float)(end - e) * inv;
+            if (PREC == 1) share = bf16_round(share);
+            u = min(__float2uint_rn(Wf * share), rem);
+        }
+        if (u) deposit_u<SMEM_RING>(s, gacc, idx, u);
+        rem -= u;
+        ++idx;
+        e += ipt;
+        ++h;
+    }
+}
+
 template <bool SMEM_TICKS, bool TAB>
 __device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                           const int32_t *trow, int j, int T, int tb, int h0) {
@@ -214,102 +243,235 @@ __device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s,
     return T + __ldg(&tick_day[tb + min(h0, p.N - 1)]);
 }
 
-// One route's forward walk: deposit f rho of every window on observed links.
-// FAST: every f of the warp lies in [0, 3000), so each deposit f * share does too.
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool FAST>
-__device__ __forceinline__ void forward_walk(const FusedParams &p, const Shared &s, const int32_t *tick_day,
-                                             const int32_t *trow, const RouteRegs &rr, float *gacc, int beta, int bb,
-                                             bool vw, float f) {
+// Forward walk of route t of a group from depth j0: every window on an
+// observed link deposits W rho, W the summed flow of the group's routes t..E
+// that share the window (exclusive prefix sums S over the group, 2^-20
+// vehicle units).  Integer form (every flow of the warp's group in
+// [0, 2^31)): the head cell gets rn(W d0) and a two-cell window's tail
+// W - rn(W d0); when the tail cell is where the next lane's window starts,
+// the next lane adds the tail to its own head deposit (one atomic per window
+// instead of two).
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                               const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
+                                               int T, bool vw, const long long *S, int t, int E, int *stk) {
+    const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.N;
-    int T = ipt * bb;
-    for (int j = 0; j < beta; ++j) {
-        const int tb = __shfl_sync(0xffffffffu, j < 32 ? rr.t0 : rr.t1, j & 31);
-        const int ob = __shfl_sync(0xffffffffu, j < 32 ? rr.o0 : rr.o1, j & 31);
+    uint32_t Wu = (uint32_t)(S[E + 1] - S[t]);
+    float Wf = __uint2float_rn(Wu);
+    for (int j = j0; j < beta; ++j) {
+        const bool first32 = j < 32;
+        const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
+        const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
+        const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
+        if ((ev >> 1) != E) {          // routes branch off: fewer of them share this window
+            E = ev >> 1;
+            Wu = (uint32_t)(S[E + 1] - S[t]);
+            Wf = __uint2float_rn(Wu);
+        }
         const int hi = __shfl_down_sync(0xffffffffu, T, 1);
         const int h0 = interval_of(T, p.div);
         if (ob != kInactive) {
+            uint32_t u0 = 0, give = 0;
+            int kind = 0;              // 1: the tail fills the next cell to its end; 2: three or more cells
+            int e0 = 0;
+            float inv = 0.f;
             if (vw && h0 < N) {
-                const int idx = ob + h0;
-                const int e0 = h0 * ipt + ipt;
-                const float inv = __fdividef(1.f, (float)(hi - T));
+                e0 = h0 * ipt + ipt;
+                inv = __fdividef(1.f, (float)(hi - T));
                 const float d0 = first_share<PREC>(T, e0, inv);
-                const float c0 = f * d0;
-                deposit<SMEM_RING, FAST>(s, gacc, idx, c0);
+                u0 = min(__float2uint_rn(Wf * d0), Wu);
                 if (hi > e0 && h0 + 1 < N) {
-                    if (hi <= e0 + ipt)
-                        deposit<SMEM_RING, FAST>(s, gacc, idx + 1, f - c0);
+                    if (hi < e0 + ipt)
+                        give = Wu - u0;
                     else
-                        window_tail<PREC, SMEM_RING, true>(s, gacc, nullptr, idx + 1, hi, e0, h0 + 1, N, ipt, inv, d0,
-                                                           f);
+                        kind = hi == e0 + ipt ? 1 : 2;
                 }
             }
+            uint32_t recv = __shfl_up_sync(0xffffffffu, give, 1);
+            if (lane == 0) recv = 0;
+            const uint32_t dep = u0 + recv;
+            if (dep) deposit_u<SMEM_RING>(s, gacc, ob + h0, dep);
+            if (kind == 1)
+                deposit_u<SMEM_RING>(s, gacc, ob + h0 + 1, Wu - u0);
+            else if (kind == 2)
+                window_tail_u<PREC, SMEM_RING>(s, gacc, ob + h0 + 1, hi, e0, h0 + 1, N, ipt, inv, Wf, Wu - u0);
         }
         T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
+        if (ev & 1) stk[j + 1] = T;
     }
 }
 
+// General form (a flow outside [0, 2^31) units): W as FP32 vehicles, one
+// 64-bit fixed-point deposit per cell.
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
-__device__ void forward_task(const FusedParams &p, const Shared &s, int day, int od, int b0,
-                             const int32_t *tab) {
+__device__ __forceinline__ void forward_walk_f(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                               const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
+                                               int T, bool vw, const long long *S, int t, int E, int *stk) {
+    const int ipt = p.div.ipt, N = p.N;
+    float f = (float)((double)(S[E + 1] - S[t]) * kFxInv);
+    for (int j = j0; j < beta; ++j) {
+        const bool first32 = j < 32;
+        const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
+        const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
+        const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
+        if ((ev >> 1) != E) {
+            E = ev >> 1;
+            f = (float)((double)(S[E + 1] - S[t]) * kFxInv);
+        }
+        const int hi = __shfl_down_sync(0xffffffffu, T, 1);
+        const int h0 = interval_of(T, p.div);
+        if (ob != kInactive && vw && h0 < N) {
+            const int idx = ob + h0;
+            const int e0 = h0 * ipt + ipt;
+            const float inv = __fdividef(1.f, (float)(hi - T));
+            const float d0 = first_share<PREC>(T, e0, inv);
+            const float c0 = f * d0;
+            deposit<SMEM_RING>(s, gacc, idx, c0);
+            if (hi > e0 && h0 + 1 < N) {
+                if (hi <= e0 + ipt)
+                    deposit<SMEM_RING>(s, gacc, idx + 1, f - c0);
+                else
+                    window_tail<PREC, SMEM_RING, true>(s, gacc, nullptr, idx + 1, hi, e0, h0 + 1, N, ipt, inv, d0, f);
+            }
+        }
+        T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
+        if (ev & 1) stk[j + 1] = T;
+    }
+}
+
+// Entry time of a route's walk at its start depth s0: the departure boundary at
+// the root, else the time stored by the walk that passed depth s0 - 1 (or the
+// repaired trajectory table).
+template <bool TAB>
+__device__ __forceinline__ int walk_start(const FusedParams &p, const int32_t *trow, const int *stk, int s0, int bb) {
+    if (s0 == 0) return p.div.ipt * bb;
+    if (TAB) return __ldg(&trow[(size_t)s0 * (p.N + 1)]);
+    return stk[s0];
+}
+
+// Forward task: walk group g for departure boundaries b0 .. b0 + 31.
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ void forward_task(const FusedParams &p, const Shared &s, int day, int g, int b0, const int32_t *tab) {
     const int lane = threadIdx.x & 31;
     const int b = b0 + lane;
     const int bb = min(b, p.N);
     const bool vw = (lane < kTileW) && (b < p.N);
     const int bi = min(b, p.N - 1);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
-    const int2 rr0 = s.odr[od];
-    const float qv = vw ? Operand<PREC>::q(p, ((size_t)day * p.K + od) * p.Np + b) : 0.f;
-    if (!__any_sync(0xffffffffu, qv != 0.f)) return;     // nothing departs: no deposits
+    const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    // route flows f = p q (Eq. (flow)) in 2^-20 vehicle units and their
+    // exclusive prefix sums over the group's walk order
+    long long S[kGroupRoutes + 1];
+    long long acc = 0;
+    bool nonneg = true, any = false;
+    S[0] = 0;
+    for (int t = 0; t < m; ++t) {
+        const int k = s.groute[i0 + t].x;
+        float f = 0.f;
+        if (vw)
+            f = __ldg(&p.pt[((size_t)day * p.P + k) * p.Np + bi]) *
+                Operand<PREC>::q(p, ((size_t)day * p.K + __ldg(&p.rod[k])) * p.Np + b);
+        const long long fu = __float2ll_rn(f * kFxScale);
+        nonneg = nonneg && fu >= 0;
+        any = any || fu != 0;
+        acc += fu;
+        S[t + 1] = acc;
+    }
+    if (!__any_sync(0xffffffffu, any)) return;            // nothing departs: no deposits
+    const bool fast = __all_sync(0xffffffffu, nonneg && acc < (1ll << 31));
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
-    for (int i = rr0.x; i < rr0.y; ++i) {
-        const int4 ri = s.rinfo[i];
-        const int k = ri.x, l0 = ri.y, beta = ri.z;
-        const float f = __ldg(&p.pt[((size_t)day * p.P + k) * p.Np + bi]) * qv;
+    int stk[kMaxRouteLinks + 1];
+    for (int t = 0; t < m; ++t) {
+        const int4 gr = s.groute[i0 + t];
+        const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        if (s0 >= beta) continue;                         // every link walked by earlier routes
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bb : nullptr;
-        if (__all_sync(0xffffffffu, f >= 0.f && f < 3000.f))
-            forward_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trow, rr, gacc, beta, bb, vw, f);
+        const int T = walk_start<TAB>(p, trow, stk, s0, bb);
+        const int E = __shfl_sync(0xffffffffu, s0 < 32 ? rr.e0 : rr.e1, s0 & 31) >> 1;
+        if (fast)
+            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t, E,
+                                                             stk);
         else
-            forward_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, false>(p, s, tick_day, trow, rr, gacc, beta, bb, vw, f);
+            forward_walk_f<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t, E,
+                                                             stk);
     }
 }
 
+// Algorithm 1's update of one (OD, departure b) from its routes' adjoint sums
+// gp_k: g = sum_k p_k gp_k (Eq. (flow) transposed).  SOLVE: Adagrad step and
+// projection max(q, 0).  LOSS_GRAD: 2 g, and the dL/dtheta terms
+// 2 q gp_k dp_k/dtheta with dp_k/dtheta = p_k sum_k' p_k' (C_k' - C_k)
+// (Eq. (logit)), route-time differences taken first to avoid cancellation.
+template <int PREC, class RouteK, class RouteGp>
+__device__ __forceinline__ void od_update(const FusedParams &p, int day, int od, int b, int nr, RouteK route_k,
+                                          RouteGp route_gp, double &dth) {
+    const float *pt = p.pt + (size_t)day * p.P * p.Np;
+    float g = 0.f;
+    for (int i = 0; i < nr; ++i) g += __ldg(&pt[(size_t)route_k(i) * p.Np + b]) * route_gp(i);
+    const size_t qi = ((size_t)day * p.K + od) * p.Np + b;
+    if (p.mode == MODE_SOLVE) {
+        const float Gv = p.G[qi] + g * g;
+        float qv = p.q[qi] - p.eta * g / (sqrtf(Gv) + p.eps);
+        qv = fmaxf(qv, 0.f);
+        p.G[qi] = Gv;
+        p.q[qi] = qv;
+        if (PREC == 1) p.qb[qi] = __float2bfloat16_rn(qv);
+    } else if (p.mode == MODE_LOSS_GRAD) {
+        p.gout[qi] = 2.f * g;
+        const float *Cd = p.C + (size_t)day * p.P * p.Np;
+        for (int i = 0; i < nr; ++i) {
+            const int k = route_k(i);
+            const float ck = Cd[(size_t)k * p.Np + b];
+            float dc = 0.f;
+            for (int i2 = 0; i2 < nr; ++i2) {
+                const int k2 = route_k(i2);
+                dc += __ldg(&pt[(size_t)k2 * p.Np + b]) * (Cd[(size_t)k2 * p.Np + b] - ck);
+            }
+            dth += 2.0 * (double)p.q[qi] * (double)route_gp(i) * (double)__ldg(&pt[(size_t)k * p.Np + b]) *
+                   (double)dc;
+        }
+    }
+}
+
+__device__ __forceinline__ void add_dtheta(double dth, double *s_dth) {
+    for (int off = 16; off > 0; off >>= 1) dth += __shfl_down_sync(0xffffffffu, dth, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(s_dth, dth);
+}
+
+// Adjoint task: the same walk gathers r over every window (B^T r at route
+// level, Algorithm 1's gradient).  A route's sum is the partial sum stored at
+// its start depth plus its own windows.  The ODs the group owns are updated
+// here; routes of other ODs leave their sums in the CTA's route slot for the
+// step pass.
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
-__device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int od, int b0, const void *rb,
+__device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int g, int b0, const void *rb,
                              const int32_t *tab, double *s_dth) {
     const int lane = threadIdx.x & 31;
     const int b = b0 + lane;
     const int bb = min(b, p.N);
     const bool vw = (lane < kTileW) && (b < p.N);
-    const int bi = min(b, p.N - 1);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
-    const int2 rr0 = s.odr[od];
     const int ipt = p.div.ipt, N = p.N;
-    const size_t qi = ((size_t)day * p.K + od) * p.Np + b;
-    const bool grad = p.mode == MODE_LOSS_GRAD;
-    const float *Cday = p.C + (size_t)day * p.P * p.Np;
-    float m = 0.f, rden = 1.f;
-    if (grad) logit_norm(p, s, Cday, rr0.x, rr0.y, bi, m, rden);
+    const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
     const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
-    float g = 0.f;
-    double dth = 0.0;
-    for (int i = rr0.x; i < rr0.y; ++i) {
-        const int4 ri = s.rinfo[i];
-        const int k = ri.x, l0 = ri.y, beta = ri.z;
-        float pk, ck = 0.f;
-        if (grad) {
-            ck = Cday[(size_t)k * p.Np + bi];
-            pk = expf(-p.theta * ck - m) * rden;
-        } else {
-            pk = __ldg(&p.pt[((size_t)day * p.P + k) * p.Np + bi]);
-        }
+    float *gp = p.gp + (size_t)blockIdx.x * p.P * p.Np;
+    int stk[kMaxRouteLinks + 1];
+    float gstk[kMaxRouteLinks + 1];
+    float gpl[kGroupRoutes];
+    for (int t = 0; t < m; ++t) {
+        const int4 gr = s.groute[i0 + t];
+        const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bb : nullptr;
-        float gp = 0.f;
-        int T = ipt * bb;
-        for (int j = 0; j < beta; ++j) {
-            const int tb = __shfl_sync(0xffffffffu, j < 32 ? rr.t0 : rr.t1, j & 31);
-            const int ob = __shfl_sync(0xffffffffu, j < 32 ? rr.o0 : rr.o1, j & 31);
+        int T = walk_start<TAB>(p, trow, stk, s0, bb);
+        float G = s0 == 0 ? 0.f : gstk[s0];
+        for (int j = s0; j < beta; ++j) {
+            const bool first32 = j < 32;
+            const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
+            const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
+            const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
             const int hi = __shfl_down_sync(0xffffffffu, T, 1);
             const int h0 = interval_of(T, p.div);
             if (ob != kInactive) {
@@ -326,35 +488,54 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
                             a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt,
                                                                      inv, d0, 0.f);
                     }
-                    gp += a;
+                    G += a;
                 }
             }
             T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
-        }
-        g += pk * gp;
-        if (grad && vw) {
-            // dp_k/dtheta = p_k (cbar - C_k) with cbar - C_k = sum_k' p_k' (C_k' - C_k):
-            // differences of route times first, which avoids the cancellation
-            float dc = 0.f;
-            for (int i2 = rr0.x; i2 < rr0.y; ++i2) {
-                const float c2 = Cday[(size_t)s.rinfo[i2].x * p.Np + bi];
-                dc += expf(-p.theta * c2 - m) * rden * (c2 - ck);
+            if (ev & 1) {
+                stk[j + 1] = T;
+                gstk[j + 1] = G;
             }
-            dth += 2.0 * (double)p.q[qi] * (double)gp * (double)pk * (double)dc;
+        }
+        gpl[t] = G;
+        if (!(gr.w >> 8) && vw) gp[(size_t)k * p.Np + b] = G;
+    }
+    const int e0 = __ldg(&p.god_ptr[g]), e1 = __ldg(&p.god_ptr[g + 1]);
+    if (e0 == e1) return;
+    double dth = 0.0;
+    if (vw) {
+        for (int e = e0; e < e1; ++e) {
+            const int r0 = __ldg(&p.godr_ptr[e]);
+            const int *gr = p.godr + r0;
+            od_update<PREC>(p, day, __ldg(&p.god[e]), b, __ldg(&p.godr_ptr[e + 1]) - r0,
+                            [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
+                            [&](int i) { return gpl[__ldg(&gr[i])]; }, dth);
         }
     }
-    if (!vw) return;
-    if (p.mode == MODE_SOLVE) {
-        const float Gv = p.G[qi] + g * g;
-        float qv = p.q[qi] - p.eta * g / (sqrtf(Gv) + p.eps);
-        qv = fmaxf(qv, 0.f);
-        p.G[qi] = Gv;
-        p.q[qi] = qv;
-        if (PREC == 1) p.qb[qi] = __float2bfloat16_rn(qv);
-    } else if (grad) {
-        p.gout[qi] = 2.f * g;
-        atomicAdd(s_dth, dth);
+    if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
+}
+
+// After a phase's adjoint tasks: the ODs whose routes span several groups
+// (only when an origin has more than kGroupRoutes routes).
+template <int PREC>
+__device__ void step_phase(const FusedParams &p, int day, int pb0, int span, double *s_dth) {
+    const float *gp = p.gp + (size_t)blockIdx.x * p.P * p.Np;
+    double dth = 0.0;
+    const int n = p.n_step_ods * span;
+    for (int x0 = 0; x0 < n; x0 += blockDim.x) {     // uniform trip count: add_dtheta shuffles the full warp
+        const int x = x0 + threadIdx.x;
+        if (x < n) {
+            const int od = __ldg(&p.step_ods[x / span]);
+            const int b = pb0 + (x - (x / span) * span);
+            if (b < p.N) {
+                const int r0 = __ldg(&p.od_ptr[od]);
+                const int *rk = p.od_routes + r0;
+                od_update<PREC>(p, day, od, b, __ldg(&p.od_ptr[od + 1]) - r0, [&](int i) { return __ldg(&rk[i]); },
+                                [&](int i) { return gp[(size_t)__ldg(&rk[i]) * p.Np + b]; }, dth);
+            }
+        }
     }
+    if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
 }
 
 __device__ __forceinline__ double block_sum(double v, double *s_red) {
@@ -592,7 +773,7 @@ __device__ int row_labels(const FusedParams &p, const uint32_t *mk, int gday, in
 }
 
 // Dynamic shared memory layout (16-byte aligned blocks):
-//   rinfo int4[P] | odr int2[K] | task_od int[K] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
+//   groute int4[P] | gptr int[G+1] | task_grp int[G] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
 __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -602,21 +783,21 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     s.pb = 0;
     auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     size_t off = 0;
-    int4 *rinfo = reinterpret_cast<int4 *>(smem_raw + off);
+    int4 *groute = reinterpret_cast<int4 *>(smem_raw + off);
     off = align16(off + (size_t)p.P * sizeof(int4));
-    int2 *odr = reinterpret_cast<int2 *>(smem_raw + off);
-    off = align16(off + (size_t)p.K * sizeof(int2));
-    int *task_od = reinterpret_cast<int *>(smem_raw + off);
-    off = align16(off + (size_t)p.K * sizeof(int));
+    int *gptr = reinterpret_cast<int *>(smem_raw + off);
+    off = align16(off + (size_t)(p.n_groups + 1) * sizeof(int));
+    int *task_grp = reinterpret_cast<int *>(smem_raw + off);
+    off = align16(off + (size_t)p.n_groups * sizeof(int));
     uint32_t *colact = reinterpret_cast<uint32_t *>(smem_raw + off);
     off = align16(off + (size_t)p.Ow * sizeof(uint32_t));
     s.lo = reinterpret_cast<uint32_t *>(smem_raw + off);
     if (SMEM_RING) off = align16(off + (size_t)p.O * s.R * sizeof(uint32_t));
     s.tw = reinterpret_cast<uint16_t *>(smem_raw + off);
     s.colact = colact;
-    s.rinfo = rinfo;
-    s.odr = odr;
-    s.task_od = task_od;
+    s.groute = groute;
+    s.gptr = gptr;
+    s.task_grp = task_grp;
     s.hi = SMEM_RING ? reinterpret_cast<int *>(p.gring) + (size_t)blockIdx.x * p.O * s.R : nullptr;
     __shared__ int s_day;
     __shared__ int s_task;
@@ -634,15 +815,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
 
     // network tables
-    for (int i = threadIdx.x; i < p.P; i += nthr) {
-        const int k = __ldg(&p.od_routes[i]);
-        const int l0 = __ldg(&p.rptr[k]);
-        rinfo[i] = make_int4(k, l0, __ldg(&p.rptr[k + 1]) - l0, 0);
-    }
-    for (int i = threadIdx.x; i < p.K; i += nthr) {
-        odr[i] = make_int2(__ldg(&p.od_ptr[i]), __ldg(&p.od_ptr[i + 1]));
-        task_od[i] = __ldg(&p.task_od[i]);
-    }
+    for (int i = threadIdx.x; i < p.P; i += nthr) groute[i] = __ldg(&p.groute[i]);
+    for (int i = threadIdx.x; i <= p.n_groups; i += nthr) gptr[i] = __ldg(&p.gptr[i]);
+    for (int i = threadIdx.x; i < p.n_groups; i += nthr) task_grp[i] = __ldg(&p.task_grp[i]);
     if (SMEM_RING) {
         for (int i = threadIdx.x; i < p.O * s.R; i += nthr) {
             s.lo[i] = 0u;
@@ -699,7 +874,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             float ks = 0.f, kc = 0.f;  // solve: compensated FP32 sum
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
-                const int ntask = nt * p.K;
+                const int ntask = nt * p.n_groups;
                 s.pb = pb0;
                 if (SMEM_TICKS && !tab) {
                     stage_ticks(p, s, tick_day);
@@ -710,12 +885,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int od = task_od[t / nt];
+                    const int g = task_grp[t / nt];
                     const int b0 = pb0 + (t % nt) * kTileW;
                     if (tab)
-                        forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, od, b0, tab);
+                        forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, tab);
                     else
-                        forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, od, b0, tab);
+                        forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, tab);
                 }
                 __syncthreads();
                 // rows [pb0, pb0 + 31 nt) are final: residual, loss, residual slot;
@@ -773,7 +948,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             // ------------------------------ adjoint sweep ------------------------------
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
-                const int ntask = nt * p.K;
+                const int ntask = nt * p.n_groups;
                 s.pb = pb0;
                 __syncthreads();                           // previous phase done with the windows
                 if (SMEM_TICKS && !tab) stage_ticks(p, s, tick_day);
@@ -784,15 +959,16 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int od = task_od[t / nt];
+                    const int g = task_grp[t / nt];
                     const int b0 = pb0 + (t % nt) * kTileW;
                     if (tab)
-                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, od, b0, rb, tab, &s_dth);
+                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, rb, tab, &s_dth);
                     else
-                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, od, b0, rb, tab, &s_dth);
+                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, rb, tab, &s_dth);
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) s_task = 0;
+                if (p.n_step_ods) step_phase<PREC>(p, day, pb0, nt * kTileW, &s_dth);
             }
             __syncthreads();
             if (SMEM_RING) {
