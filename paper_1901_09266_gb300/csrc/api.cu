@@ -48,6 +48,7 @@ struct dode_ctx {
     // days
     int D = 0;
     int32_t *d_ticks = nullptr;
+    uint16_t *d_ticks16 = nullptr;
     float *d_counts = nullptr;
     uint32_t *d_mask = nullptr, *d_colact = nullptr;
     float *d_C = nullptr;
@@ -507,6 +508,7 @@ FusedParams base_params(dode_ctx *ctx) {
     p.n_step_ods = (int)ctx->step_ods.size();
     p.pt = ctx->d_pt;
     p.ticks = ctx->d_ticks;
+    p.ticks16 = ctx->d_ticks16;
     p.counts = ctx->d_counts;
     p.mask = ctx->d_mask;
     p.colact = ctx->d_colact;
@@ -564,6 +566,7 @@ void drop_graph(dode_ctx *ctx) {
 void free_days(dode_ctx *ctx) {
     drop_graph(ctx);
     dfree(ctx->d_ticks);
+    dfree(ctx->d_ticks16);
     dfree(ctx->d_counts);
     dfree(ctx->d_mask);
     dfree(ctx->d_colact);
@@ -980,6 +983,7 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
     if (D != ctx->D) {
         free_days(ctx);
         CU(dalloc(&ctx->d_ticks, (size_t)D * A * Np));
+        CU(dalloc(&ctx->d_ticks16, (size_t)D * A * Np));
         CU(dalloc(&ctx->d_counts, (size_t)D * O * Np));
         CU(dalloc(&ctx->d_mask, (size_t)D * O * ctx->Nw));
         CU(dalloc(&ctx->d_colact, (size_t)D * ctx->Ow));
@@ -1010,8 +1014,8 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
     rc = input(ctx, speeds, sp_bytes, ptr_kind, 0, &dsp);
     if (rc) return rc;
     CU(cudaMemsetAsync(ctx->d_err, 0, 4 * sizeof(int), ctx->stream));
-    CUL(launch_ticks(static_cast<const float *>(dsp), ctx->d_len, D, N, Np, A, ctx->tps, ctx->d_ticks, ctx->d_err + 3,
-                     ctx->d_err, ctx->stream));
+    CUL(launch_ticks(static_cast<const float *>(dsp), ctx->d_len, D, N, Np, A, ctx->tps, ctx->d_ticks,
+                     ctx->d_ticks16, ctx->d_err + 3, ctx->d_err, ctx->stream));
     CU(cudaMemcpyAsync(&ctx->max_tick, ctx->d_err + 3, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     rc = check_device_error(ctx);
     if (rc) {

@@ -81,6 +81,7 @@ struct FusedParams {
     const float *pt;           // [D][P][Np] route choice for the call's theta
     // per-day inputs
     const int32_t *ticks;
+    const uint16_t *ticks16;   // [D][A][Np] 16-bit copy, entries >= N repeat row N-1 (tick windows)
     const float *counts;
     const uint32_t *mask;
     const uint32_t *colact;
@@ -161,7 +162,7 @@ __device__ __forceinline__ void set_error(int *err, int code, long long index) {
 
 // launchers (defined in the .cu files)
 cudaError_t launch_ticks(const float *speeds, const float *len, int D, int N, int Np, int A, int tps,
-                         int32_t *ticks, int *maxtick, int *err, cudaStream_t s);
+                         int32_t *ticks, uint16_t *ticks16, int *maxtick, int *err, cudaStream_t s);
 cudaError_t launch_prepare(const PrepParams &p, cudaStream_t s);
 cudaError_t launch_transpose_in(const float *src, float *dst, int D, int N, int Np, int M,
                                 cudaStream_t s);  // [D][N][M] -> [D][M][Np]

@@ -552,48 +552,85 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
     return t;  // valid in thread 0
 }
 
-// Tick rows [pb, pb + RW) of every link; rows past the end of the day repeat the
-// last interval (the link entry rule clamps to it).  Each warp loads four
-// links' rows before storing, to keep many loads in flight.
-__device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, const int32_t *tick_day) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int a0 = warp; a0 < p.A; a0 += 4 * nw) {
-        for (int r0 = 0; r0 < s.RW; r0 += 32) {
-            const int r = r0 + lane;
-            int v[4];
+// Tick rows [pb, pb + RW) of every link from the 16-bit table, whose entries
+// past the end of the day repeat the last interval (the link entry rule clamps
+// to it).  16-byte loads of 8 ticks at 8-aligned row positions, four per
+// thread in flight before the shared stores; chunks past the table row take
+// the last interval's value.
+__device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, const uint16_t *t16) {
+    const int c0 = s.pb & ~7;
+    const int nch = (s.pb + s.RW - c0 + 7) >> 3;       // 8-tick chunks per link
+    const int total = p.A * nch;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+        uint4 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int a = a0 + u * nw;
-                v[u] = (a < p.A && r < s.RW) ? __ldg(&tick_day[(size_t)a * p.Np + min(s.pb + r, p.N - 1)]) : 0;
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (i < total) {
+                const int a = i / nch, c = c0 + 8 * (i - a * nch);
+                const uint16_t *row = t16 + (size_t)a * p.Np;
+                if (c + 8 <= p.Np) {
+                    v[u] = __ldg(reinterpret_cast<const uint4 *>(row + c));
+                } else {
+                    uint32_t x = __ldg(row + p.Np - 1);
+                    x |= x << 16;
+                    v[u] = make_uint4(x, x, x, x);
+                }
             }
+        }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int a = a0 + u * nw;
-                if (a < p.A && r < s.RW) s.tw[a * s.RW + r] = (uint16_t)v[u];
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < total) {
+                const int a = i / nch, c = c0 + 8 * (i - a * nch);
+                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                uint16_t *row = s.tw + a * s.RW;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int r = c + k - s.pb;
+                    if (r >= 0 && r < s.RW) row[r] = (uint16_t)(w[k >> 1] >> ((k & 1) * 16));
+                }
             }
         }
     }
 }
 
 // Residual rows [pb, pb + R) (clipped to the day) of every observed link, as
-// float bits in the accumulator array.
+// float bits in the accumulator array: 16-byte loads (8 BF16 or 4 FP32
+// residuals) at aligned row positions, four per thread in flight.
 template <int PREC>
 __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, const void *rb) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    constexpr int E = PREC == 1 ? 8 : 4;              // residuals per 16 bytes
     const int rows = min(s.R, p.N - s.pb);
-    for (int o0 = warp; o0 < p.O; o0 += 4 * nw) {
-        for (int r0 = 0; r0 < rows; r0 += 32) {
-            const int r = r0 + lane;
-            float v[4];
+    const int c0 = s.pb & ~(E - 1);
+    const int nch = (s.pb + rows - c0 + E - 1) / E;
+    const int total = p.O * nch;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
+        uint4 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int o = o0 + u * nw;
-                v[u] = (o < p.O && r < rows) ? Operand<PREC>::r(rb, (size_t)o * p.Np + s.pb + r) : 0.f;
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            v[u] = make_uint4(0u, 0u, 0u, 0u);
+            if (i < total) {
+                const int o = i / nch, c = c0 + E * (i - o * nch);
+                v[u] = __ldg(reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(rb) +
+                                                            ((size_t)o * p.Np + c) * (PREC == 1 ? 2 : 4)));
             }
+        }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int o = o0 + u * nw;
-                if (o < p.O && r < rows) s.lo[o * s.R + r] = __float_as_uint(v[u]);
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < total) {
+                const int o = i / nch, c = c0 + E * (i - o * nch);
+                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                uint32_t *row = s.lo + o * s.R;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int r = c + k - s.pb;
+                    const uint32_t bits = PREC == 1 ? (k & 1 ? (w[k >> 1] & 0xffff0000u) : (w[k >> 1] << 16)) : w[k];
+                    if (r >= 0 && r < rows) row[r] = bits;
+                }
             }
         }
     }
@@ -675,6 +712,70 @@ __device__ __forceinline__ void flush_phase(const FusedParams &p, const Shared &
                         Operand<PREC>::store_r(rb, ri, use ? rr : 0.f);
                     }
                 }
+            }
+        }
+    }
+}
+
+// Solve-path flush of a phase (the !EXACT case of flush_phase), four rows per
+// thread: 16-byte loads of counts (and row-chunk labels) at 4-aligned row
+// positions, one mask word, 8- or 16-byte residual stores.
+template <int PREC, bool SMEM_RING>
+__device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &s, float *gacc, void *rb,
+                                            const float *cnt, const uint32_t *mk, const int32_t *lab, int sel, int pb0,
+                                            int rows, bool carry, float &ks, float &kc) {
+    const int c0 = pb0 & ~3;
+    const int nch = (pb0 + rows - c0 + 3) >> 2;
+    const int total = p.O * nch;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int o = i / nch, c = c0 + 4 * (i - o * nch);
+        const size_t cell = (size_t)o * p.Np + c;
+        const float4 cv = __ldg(reinterpret_cast<const float4 *>(cnt + cell));
+        const uint32_t mw = (__ldg(&mk[(size_t)o * p.Nw + (c >> 5)]) >> (c & 31)) & 0xfu;
+        int4 lv = make_int4(0, 0, 0, 0);
+        if (sel >= 0) lv = __ldg(reinterpret_cast<const int4 *>(lab + cell));
+        const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+        const int ll[4] = {lv.x, lv.y, lv.z, lv.w};
+        float r4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = c + k - pb0;
+            const bool in = r >= 0 && r < rows;
+            float x = 0.f;
+            if (in) {
+                if (SMEM_RING) {
+                    const int idx = o * s.R + r;
+                    const int hw = carry ? s.hi[idx] : 0;
+                    x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
+                } else {
+                    x = gacc[cell + k];
+                    gacc[cell + k] = 0.f;
+                }
+            }
+            const bool on = in && ((mw >> k) & 1u);
+            const float rr = on ? x - cc[k] : 0.f;
+            const float y = rr * rr - kc;          // compensated (Kahan) sum
+            const float t = ks + y;
+            kc = (t - ks) - y;
+            ks = t;
+            r4[k] = (sel < 0 || (on && ll[k] == sel)) ? rr : 0.f;
+        }
+        if (c >= pb0 && c + 4 <= pb0 + rows) {
+            if (PREC == 1) {
+                __nv_bfloat162 lo2 = __floats2bfloat162_rn(r4[0], r4[1]);
+                __nv_bfloat162 hi2 = __floats2bfloat162_rn(r4[2], r4[3]);
+                uint2 pk;
+                pk.x = *reinterpret_cast<uint32_t *>(&lo2);
+                pk.y = *reinterpret_cast<uint32_t *>(&hi2);
+                *reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(rb) + cell) = pk;
+            } else {
+                *reinterpret_cast<float4 *>(static_cast<float *>(rb) + cell) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int r = c + k - pb0;
+                if (r >= 0 && r < rows) Operand<PREC>::store_r(rb, cell + k, r4[k]);
             }
         }
     }
@@ -842,6 +943,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         const int64_t toff = p.tab_off[day];
         const int32_t *tab = toff >= 0 ? p.traj_tab + toff : nullptr;
         const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
+        const uint16_t *tick16_day = p.ticks16 + (size_t)day * p.A * p.Np;
         const float *cnt = p.counts + (size_t)day * p.O * p.Np;
         const uint32_t *mk = p.mask + (size_t)day * p.O * p.Nw;
         const int maxoff = p.maxoff[day];
@@ -877,7 +979,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 const int ntask = nt * p.n_groups;
                 s.pb = pb0;
                 if (SMEM_TICKS && !tab) {
-                    stage_ticks(p, s, tick_day);
+                    stage_ticks(p, s, tick16_day);
                     __syncthreads();
                 }
                 while (true) {
@@ -902,8 +1004,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     flush_phase<PREC, SMEM_RING, true>(p, s, gacc, rb, cnt, mk, lab, sel, day, pb0, rows, carry, lsum,
                                                        ks, kc);
                 else
-                    flush_phase<PREC, SMEM_RING, false>(p, s, gacc, rb, cnt, mk, lab, sel, day, pb0, rows, carry,
-                                                        lsum, ks, kc);
+                    flush_solve<PREC, SMEM_RING>(p, s, gacc, rb, cnt, mk, lab, sel, pb0, rows, carry, ks, kc);
                 if (SMEM_RING) {
                     // move the spill rows [span, span + spill) to the front, zero the rest
                     __syncthreads();
@@ -951,7 +1052,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 const int ntask = nt * p.n_groups;
                 s.pb = pb0;
                 __syncthreads();                           // previous phase done with the windows
-                if (SMEM_TICKS && !tab) stage_ticks(p, s, tick_day);
+                if (SMEM_TICKS && !tab) stage_ticks(p, s, tick16_day);
                 if (SMEM_RING) stage_residual<PREC>(p, s, rb);
                 __syncthreads();
                 while (true) {

@@ -13,8 +13,18 @@ namespace dode {
 // 32 x 32 tiles are transposed through shared memory: reads run along links,
 // writes along intervals.
 // ---------------------------------------------------------------------------
+// Link travel time in ticks at speed v (Eq. (cost)): rint(fl32(fl32(len * 3600 tps) / v)), at least 1;
+// 0 marks an invalid speed or an overflow.
+__device__ __forceinline__ int32_t tick_of(float len, float scale, float v) {
+    if (!(v > 0.f) || !isfinite(v)) return 0;
+    const float t = __fdiv_rn(__fmul_rn(len, scale), v);
+    if (!(t <= 16777216.f)) return 0;
+    return max(__float2int_rn(t), 1);
+}
+
 __global__ void k_ticks(const float *__restrict__ speeds, const float *__restrict__ len, int N, int Np,
-                        int A, float scale, int32_t *__restrict__ ticks, int *maxtick, int *err) {
+                        int A, float scale, int32_t *__restrict__ ticks, uint16_t *__restrict__ ticks16, int *maxtick,
+                        int *err) {
     __shared__ int32_t tile[32][33];
     const int d = blockIdx.z;
     const int a0 = blockIdx.x * 32, h0 = blockIdx.y * 32;
@@ -40,6 +50,7 @@ __global__ void k_ticks(const float *__restrict__ speeds, const float *__restric
     }
     __syncthreads();
     int32_t *tk = ticks + (size_t)d * A * Np;
+    uint16_t *tk16 = ticks16 + (size_t)d * A * Np;
     int mx = 0;
     for (int i = threadIdx.y; i < 32; i += blockDim.y) {
         const int a = a0 + i, h = h0 + threadIdx.x;
@@ -47,6 +58,11 @@ __global__ void k_ticks(const float *__restrict__ speeds, const float *__restric
             const int32_t c = h < N ? tile[threadIdx.x][i] : 1;
             tk[(size_t)a * Np + h] = c;
             mx = max(mx, c);
+            // 16-bit copy for the fused kernel's tick windows: entries past the end
+            // of the day repeat the last interval (the link entry rule clamps to
+            // it); values above 16 bits saturate and the kernel does not use it
+            const int32_t c16 = h < N ? c : max(tick_of(len[a], scale, sp[(size_t)(N - 1) * A + a]), 1);
+            tk16[(size_t)a * Np + h] = (uint16_t)min(c16, 65535);
         }
     }
     for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
@@ -54,9 +70,9 @@ __global__ void k_ticks(const float *__restrict__ speeds, const float *__restric
 }
 
 cudaError_t launch_ticks(const float *speeds, const float *len, int D, int N, int Np, int A, int tps,
-                         int32_t *ticks, int *maxtick, int *err, cudaStream_t s) {
+                         int32_t *ticks, uint16_t *ticks16, int *maxtick, int *err, cudaStream_t s) {
     dim3 block(32, 8), grid((A + 31) / 32, (Np + 31) / 32, D);
-    k_ticks<<<grid, block, 0, s>>>(speeds, len, N, Np, A, (float)(tps * 3600), ticks, maxtick, err);
+    k_ticks<<<grid, block, 0, s>>>(speeds, len, N, Np, A, (float)(tps * 3600), ticks, ticks16, maxtick, err);
     return cudaGetLastError();
 }
 
