@@ -32,7 +32,7 @@ struct dode_ctx {
     std::vector<int2> rpack;                           // (link, observed column) per route position
     int2 *d_rpack = nullptr;
     // walk groups of the fused kernel (routes from one origin, lexicographic order)
-    std::vector<int4> groute;                          // [P] (route, first position, links, start depth)
+    std::vector<int4> groute;                          // [P] (route, first position, links, start depth | flags)
     std::vector<int32_t> gptr, task_grp, rev;          // [G+1], [G], [L]
     std::vector<int32_t> god_ptr, god, godr_ptr, godr;  // ODs owned by each group and their routes
     std::vector<int32_t> step_ods;                     // ODs of groups that do not own them
@@ -455,6 +455,7 @@ void build_groups(dode_ctx *ctx, const int32_t *link_tail) {
     }
     for (int x = 0; x < P; ++x)        // bit 8 of the start-depth word: the group owns the route's OD
         if (owner[ctx->rod[ctx->groute[x].x]] == gof[ctx->groute[x].x]) ctx->groute[x].w |= 1 << 8;
+    for (int x = 0; x < P; ++x) ctx->groute[x].w |= ctx->rod[ctx->groute[x].x] << 9;   // bits 9..: the OD
     ctx->god_ptr.assign(1, 0);
     ctx->godr_ptr.assign(1, 0);
     for (int g = 0; g < ctx->G; ++g) {
@@ -815,6 +816,7 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     }
     for (int od = 0; od < K; ++od)
         if (od_count[od] == 0) return bail(DODE_ERR_ARG, "OD pair without a route: " + std::to_string(od));
+    if (K >= (1 << 22)) return bail(DODE_ERR_ARG, "at most 2^22 - 1 OD pairs");
 
     ctx->opt = o;
     ctx->N = o.n_intervals;

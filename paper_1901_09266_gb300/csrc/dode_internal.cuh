@@ -66,7 +66,7 @@ struct FusedParams {
     const int32_t *od_routes;  // [P] routes grouped by OD
     const int32_t *task_od;    // [K] OD processing order (largest work first)
     const int2 *rpack;         // [L] (link, observed column or -1) of every route position
-    const int4 *groute;        // [P] walk order: (route, first position, links, start depth)
+    const int4 *groute;        // [P] walk order: (route, first position, links, start depth | own << 8 | OD << 9)
     const int32_t *gptr;       // [G+1] routes of each walk group in groute
     const int32_t *task_grp;   // [G] group processing order (largest walk first)
     const int32_t *rev;        // [L] (E << 1) | save of every route position (see build_groups)

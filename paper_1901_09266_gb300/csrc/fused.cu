@@ -250,8 +250,12 @@ __device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s,
 // [0, 2^31)): the head cell gets rn(W d0) and a two-cell window's tail
 // W - rn(W d0); when the tail cell is where the next lane's window starts,
 // the next lane adds the tail to its own head deposit (one atomic per window
-// instead of two).
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+// instead of two).  On the shared ring no lane needs a range check: lanes
+// outside the tile carry W = 0, and cells past the end of the day fall in
+// ring rows that are never flushed and are cleared after the sweep.  LONG:
+// the route has more than 32 links (positions 32.. sit in the second register
+// set).
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
 __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
                                                int T, bool vw, const long long *S, int t, int E, int *stk) {
@@ -260,7 +264,7 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
     uint32_t Wu = (uint32_t)(S[E + 1] - S[t]);
     float Wf = __uint2float_rn(Wu);
     for (int j = j0; j < beta; ++j) {
-        const bool first32 = j < 32;
+        const bool first32 = !LONG || j < 32;
         const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
         const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
         const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
@@ -276,12 +280,12 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
             int kind = 0;              // 1: the tail fills the next cell to its end; 2: three or more cells
             int e0 = 0;
             float inv = 0.f;
-            if (vw && h0 < N) {
+            if (SMEM_RING || (vw && h0 < N)) {
                 e0 = h0 * ipt + ipt;
                 inv = __fdividef(1.f, (float)(hi - T));
                 const float d0 = first_share<PREC>(T, e0, inv);
                 u0 = min(__float2uint_rn(Wf * d0), Wu);
-                if (hi > e0 && h0 + 1 < N) {
+                if (hi > e0 && (SMEM_RING || h0 + 1 < N)) {
                     if (hi < e0 + ipt)
                         give = Wu - u0;
                     else
@@ -304,14 +308,14 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
 
 // General form (a flow outside [0, 2^31) units): W as FP32 vehicles, one
 // 64-bit fixed-point deposit per cell.
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
 __device__ __forceinline__ void forward_walk_f(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
                                                int T, bool vw, const long long *S, int t, int E, int *stk) {
     const int ipt = p.div.ipt, N = p.N;
     float f = (float)((double)(S[E + 1] - S[t]) * kFxInv);
     for (int j = j0; j < beta; ++j) {
-        const bool first32 = j < 32;
+        const bool first32 = !LONG || j < 32;
         const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
         const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
         const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
@@ -366,17 +370,28 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
     long long acc = 0;
     bool nonneg = true, any = false;
     S[0] = 0;
-    for (int t = 0; t < m; ++t) {
-        const int k = s.groute[i0 + t].x;
-        float f = 0.f;
-        if (vw)
-            f = __ldg(&p.pt[((size_t)day * p.P + k) * p.Np + bi]) *
-                Operand<PREC>::q(p, ((size_t)day * p.K + __ldg(&p.rod[k])) * p.Np + b);
-        const long long fu = __float2ll_rn(f * kFxScale);
-        nonneg = nonneg && fu >= 0;
-        any = any || fu != 0;
-        acc += fu;
-        S[t + 1] = acc;
+    for (int t0 = 0; t0 < m; t0 += 4) {                   // four routes' loads in flight
+        float pv[4], qv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            pv[u] = 0.f;
+            qv[u] = 0.f;
+            if (vw && t0 + u < m) {
+                const int4 gr = s.groute[i0 + t0 + u];
+                pv[u] = __ldg(&p.pt[((size_t)day * p.P + gr.x) * p.Np + bi]);
+                qv[u] = Operand<PREC>::q(p, ((size_t)day * p.K + (gr.w >> 9)) * p.Np + b);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (t0 + u < m) {
+                const long long fu = __float2ll_rn(pv[u] * qv[u] * kFxScale);
+                nonneg = nonneg && fu >= 0;
+                any = any || fu != 0;
+                acc += fu;
+                S[t0 + u + 1] = acc;
+            }
+        }
     }
     if (!__any_sync(0xffffffffu, any)) return;            // nothing departs: no deposits
     const bool fast = __all_sync(0xffffffffu, nonneg && acc < (1ll << 31));
@@ -390,12 +405,15 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
         const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bb : nullptr;
         const int T = walk_start<TAB>(p, trow, stk, s0, bb);
         const int E = __shfl_sync(0xffffffffu, s0 < 32 ? rr.e0 : rr.e1, s0 & 31) >> 1;
-        if (fast)
-            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t, E,
-                                                             stk);
+        if (fast && beta <= 32)
+            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB, false>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S,
+                                                                    t, E, stk);
+        else if (fast)
+            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t,
+                                                                   E, stk);
         else
-            forward_walk_f<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t, E,
-                                                             stk);
+            forward_walk_f<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t,
+                                                                   E, stk);
     }
 }
 
@@ -440,6 +458,49 @@ __device__ __forceinline__ void add_dtheta(double dth, double *s_dth) {
     if ((threadIdx.x & 31) == 0) atomicAdd(s_dth, dth);
 }
 
+// Adjoint walk of one route from depth j0: gathers r over every window on an
+// observed link into the running route sum G.  On the shared ring no lane
+// needs a range check: residual rows past the end of the day are staged as
+// zeros, and lanes outside the tile never store their sums.
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
+__device__ __forceinline__ float adjoint_walk(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                              const int32_t *trow, const RouteRegs &rr, const void *rb, int j0,
+                                              int beta, int T, float G, bool vw, int *stk, float *gstk) {
+    const int ipt = p.div.ipt, N = p.N;
+    const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
+    for (int j = j0; j < beta; ++j) {
+        const bool first32 = !LONG || j < 32;
+        const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
+        const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
+        const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
+        const int hi = __shfl_down_sync(0xffffffffu, T, 1);
+        const int h0 = interval_of(T, p.div);
+        if (ob != kInactive) {
+            if (SMEM_RING || (vw && h0 < N)) {
+                const int idx = ob + h0;
+                const int e0 = h0 * ipt + ipt;
+                const float inv = __fdividef(1.f, (float)(hi - T));
+                const float d0 = first_share<PREC>(T, e0, inv);
+                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                if (hi > e0 && (SMEM_RING || h0 + 1 < N)) {
+                    if (hi <= e0 + ipt)
+                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                    else
+                        a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt, inv,
+                                                                 d0, 0.f);
+                }
+                G += a;
+            }
+        }
+        T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
+        if (ev & 1) {
+            stk[j + 1] = T;
+            gstk[j + 1] = G;
+        }
+    }
+    return G;
+}
+
 // Adjoint task: the same walk gathers r over every window (B^T r at route
 // level, Algorithm 1's gradient).  A route's sum is the partial sum stored at
 // its start depth plus its own windows.  The ODs the group owns are updated
@@ -453,9 +514,8 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
     const int bb = min(b, p.N);
     const bool vw = (lane < kTileW) && (b < p.N);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
-    const int ipt = p.div.ipt, N = p.N;
+    const int N = p.N;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
-    const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
     float *gp = p.gp + (size_t)blockIdx.x * p.P * p.Np;
     int stk[kMaxRouteLinks + 1];
     float gstk[kMaxRouteLinks + 1];
@@ -465,40 +525,15 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bb : nullptr;
-        int T = walk_start<TAB>(p, trow, stk, s0, bb);
-        float G = s0 == 0 ? 0.f : gstk[s0];
-        for (int j = s0; j < beta; ++j) {
-            const bool first32 = j < 32;
-            const int tb = __shfl_sync(0xffffffffu, first32 ? rr.t0 : rr.t1, j & 31);
-            const int ob = __shfl_sync(0xffffffffu, first32 ? rr.o0 : rr.o1, j & 31);
-            const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
-            const int hi = __shfl_down_sync(0xffffffffu, T, 1);
-            const int h0 = interval_of(T, p.div);
-            if (ob != kInactive) {
-                if (vw && h0 < N) {
-                    const int idx = ob + h0;
-                    const int e0 = h0 * ipt + ipt;
-                    const float inv = __fdividef(1.f, (float)(hi - T));
-                    const float d0 = first_share<PREC>(T, e0, inv);
-                    float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
-                    if (hi > e0 && h0 + 1 < N) {
-                        if (hi <= e0 + ipt)
-                            a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
-                        else
-                            a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt,
-                                                                     inv, d0, 0.f);
-                    }
-                    G += a;
-                }
-            }
-            T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
-            if (ev & 1) {
-                stk[j + 1] = T;
-                gstk[j + 1] = G;
-            }
-        }
+        const int T = walk_start<TAB>(p, trow, stk, s0, bb);
+        const float G0 = s0 == 0 ? 0.f : gstk[s0];
+        const float G = beta <= 32
+                            ? adjoint_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, false>(p, s, tick_day, trow, rr, rb, s0,
+                                                                                   beta, T, G0, vw, stk, gstk)
+                            : adjoint_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trow, rr, rb, s0,
+                                                                                  beta, T, G0, vw, stk, gstk);
         gpl[t] = G;
-        if (!(gr.w >> 8) && vw) gp[(size_t)k * p.Np + b] = G;
+        if (!((gr.w >> 8) & 1) && vw) gp[(size_t)k * p.Np + b] = G;
     }
     const int e0 = __ldg(&p.god_ptr[g]), e1 = __ldg(&p.god_ptr[g + 1]);
     if (e0 == e1) return;
@@ -596,9 +631,10 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
     }
 }
 
-// Residual rows [pb, pb + R) (clipped to the day) of every observed link, as
-// float bits in the accumulator array: 16-byte loads (8 BF16 or 4 FP32
-// residuals) at aligned row positions, four per thread in flight.
+// Residual rows [pb, pb + R) of every observed link, as float bits in the
+// accumulator array (rows past the end of the day are zero): 16-byte loads
+// (8 BF16 or 4 FP32 residuals) at aligned row positions, four per thread in
+// flight.
 template <int PREC>
 __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, const void *rb) {
     constexpr int E = PREC == 1 ? 8 : 4;              // residuals per 16 bytes
@@ -633,6 +669,12 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
                 }
             }
         }
+    }
+    // rows past the end of the day gather nothing
+    const int tail = s.R - rows;
+    for (int i = threadIdx.x; i < p.O * tail; i += blockDim.x) {
+        const int o = i / tail;
+        s.lo[o * s.R + rows + (i - o * tail)] = 0u;
     }
 }
 
@@ -1033,6 +1075,16 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     }
                 }
                 if (threadIdx.x == 0) s_task = 0;
+                __syncthreads();
+            }
+            if (SMEM_RING) {
+                // the last phase's spill rows lie past the end of the day: clear them
+                const bool carry = s_carry != 0;
+                for (int i = threadIdx.x; i < p.O * spill; i += nthr) {
+                    const int o = i / spill, idx = o * s.R + (i - o * spill);
+                    s.lo[idx] = 0u;
+                    if (carry) s.hi[idx] = 0;
+                }
                 __syncthreads();
             }
             const double loss_day = block_sum(exact ? lsum : (double)ks - (double)kc, s_red);
