@@ -196,6 +196,49 @@ int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, flo
                    double *dtheta, int32_t ptr_kind);
 
 /*
+ * dode_set_patterns -- traffic patterns of the loaded days (Step 2-3 of the
+ * framework, Sec. 4; Eq. (logit) computes a pattern's route choice from the
+ * mean travel time of each path over the pattern's days).
+ *   pattern  [D] host: pattern label of each loaded day (>= 0), or -1 for a day
+ *            whose route choice uses its own travel times; NULL clears all
+ *            labels (every day uses its own, the default)
+ * From then on every call (solve, forward, loss, gradients) takes the route
+ * choice of day d from the mean, over the days with d's label, of the route
+ * times C_k(h) (FP64 sums in day order); dL/dtheta differentiates that route
+ * choice.  Labels are cleared by dode_set_days.  Clustering the days is the
+ * caller's (Sec. 3.1).  Errors: DODE_ERR_STATE, DODE_ERR_ARG (a label < -1),
+ * DODE_ERR_CUDA / DODE_ERR_OOM.
+ */
+int dode_set_patterns(dode_ctx *ctx, const int32_t *pattern);
+
+/*
+ * dode_r2 -- goodness of fit of Step 6 ("Quality check", Sec. 4; the case study
+ * reports the average R-square between observed and estimated link flow,
+ * Sec. 5): per day, R^2 = 1 - SS_res / SS_tot over the observed cells, with
+ * SS_res = sum m (xhat - x)^2 for OD flows q and logit dispersion theta, and
+ * SS_tot = sum m (x - xbar)^2 about the day's masked mean count xbar.
+ *   q   [D][N][n_od] FP32 (ptr_kind)
+ *   r2  [D] FP64 (ptr_kind); NaN for a day with no observed cell or constant
+ *       observed counts (SS_tot = 0)
+ * Errors: DODE_ERR_STATE, DODE_ERR_ARG, DODE_ERR_CUDA / DODE_ERR_OOM.
+ */
+int dode_r2(dode_ctx *ctx, const float *q, float theta, double *r2, int32_t ptr_kind);
+
+/*
+ * dode_dar_distance -- stability of the DAR across days (Sec. 5: the l2
+ * distance between each day's DAR matrix of Eq. (dar) and the average DAR
+ * matrix, whose histogram the paper plots).  The DAR of a day holds rho for
+ * every (route, link position, departure interval h1, arrival interval h2)
+ * with h2 before the end of the day; the mean is taken over the loaded days.
+ *   dist     [D] ||rho_d - mean rho||_F, FP64, host
+ *   mean_sq  ||mean rho||_F^2, FP64, host, may be NULL
+ * Shares are computed in FP32, sums in FP64 in a fixed order.  Works on the
+ * loaded days' speeds only; the solver state is untouched.
+ * Errors: DODE_ERR_STATE, DODE_ERR_ARG, DODE_ERR_CUDA / DODE_ERR_OOM.
+ */
+int dode_dar_distance(dode_ctx *ctx, double *dist, double *mean_sq);
+
+/*
  * dode_loss_static_scratch -- the per-day loss of dode_loss for the loaded days,
  * computed without allocating any device memory.  The paper has no counterpart:
  * this serves callers that cannot call cudaMalloc once running (a real-time or

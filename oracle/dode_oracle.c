@@ -72,6 +72,8 @@ typedef struct {
     or_dar_entry *dar;    /* DAR entries */
     int64_t n_dar;
     double *C;            /* [N][P] route time of departure interval h1, minutes */
+    double *Cc;           /* [N][P] travel times the route choice uses: this day's C,
+                             or a traffic pattern's mean (Eq. (logit)) */
     double theta;
     double *p;            /* [N][P] route choice portion */
     /* assignment matrix B (Eq. (assign)) in COO, observed rows only */
@@ -261,8 +263,17 @@ static void assemble_B(or_day *d) {
 /* Route-choice portions for a dispersion theta (per minute); rebuilds B.   */
 void or_day_set_theta(or_day *d, double theta) {
     d->theta = theta;
-    route_choice(d->net, d->C, theta, d->p);
+    route_choice(d->net, d->Cc, theta, d->p);
     assemble_B(d);
+}
+
+/* Travel times of the route choice (Eq. (logit) takes the mean travel time */
+/* of each path over the days of a traffic pattern): Cc [N][P] minutes, or  */
+/* NULL for this day's own route times.  Recomputes p and B.                */
+void or_day_set_choice_times(or_day *d, const double *Cc) {
+    const or_net *n = d->net;
+    memcpy(d->Cc, Cc ? Cc : d->C, sizeof(double) * (size_t)n->N * n->P);
+    or_day_set_theta(d, d->theta);
 }
 
 /* Build one day's model from its speeds [N][A].  Returns NULL on error.     */
@@ -284,6 +295,7 @@ or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int 
     dar_emit(n, d->T, d->dar);
     /* route time in minutes (Eq. (cost)): end of route minus departure */
     d->C = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
+    d->Cc = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
     d->p = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
     for (int32_t k = 0; k < n->P; ++k) {
         int32_t beta = n->rptr[k + 1] - n->rptr[k];
@@ -291,6 +303,7 @@ or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int 
             d->C[(size_t)h * n->P + k] =
                 (double)(d->T[traj_index(n, k, beta, h)] - (int64_t)n->ipt * h) / (double)(60 * n->tps);
     }
+    memcpy(d->Cc, d->C, sizeof(double) * (size_t)n->N * n->P);
     or_day_set_theta(d, theta);
     if (err) *err = OR_OK;
     return d;
@@ -298,7 +311,7 @@ or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int 
 
 void or_day_destroy(or_day *d) {
     if (!d) return;
-    free(d->ticks); free(d->T); free(d->dar); free(d->C); free(d->p);
+    free(d->ticks); free(d->T); free(d->dar); free(d->C); free(d->Cc); free(d->p);
     free(d->b_row); free(d->b_col); free(d->b_val);
     free(d);
 }
@@ -473,6 +486,34 @@ double or_solve_day(const or_day *d, const float *counts, const uint8_t *mask, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* Quality check (Step 6 of the framework, Sec. 4; the case study reports   */
+/* the R-square between observed and estimated link flow, Sec. 5):          */
+/* R^2 = 1 - SS_res / SS_tot over the observed cells, SS_res the masked     */
+/* loss of q, SS_tot the squared deviations of the observed counts from     */
+/* their mean.  NaN when SS_tot = 0 (no observed cell, or constant counts). */
+/* ------------------------------------------------------------------------ */
+double or_r2_day(const or_day *d, const float *counts, const uint8_t *mask, const double *q) {
+    const or_net *n = d->net;
+    size_t rows = (size_t)n->N * n->O;
+    double *xhat = (double *)malloc(sizeof(double) * rows);
+    double *r = (double *)malloc(sizeof(double) * rows);
+    or_forward(d, q, xhat);
+    double ss_res = or_residual(d, xhat, counts, mask, r);
+    double sum = 0.0, cnt = 0.0;
+    for (size_t i = 0; i < rows; ++i)
+        if (mask[i]) {
+            sum += counts[i];
+            cnt += 1.0;
+        }
+    double mean = cnt > 0.0 ? sum / cnt : 0.0, ss_tot = 0.0;
+    for (size_t i = 0; i < rows; ++i)
+        if (mask[i]) ss_tot += ((double)counts[i] - mean) * ((double)counts[i] - mean);
+    free(xhat);
+    free(r);
+    return ss_tot > 0.0 ? 1.0 - ss_res / ss_tot : NAN;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Differentiable form: L(q, theta) = sum m (B q - x)^2.                     */
 /* dL/dq = 2 B^T r;  dL/dtheta through p = logit(-theta C) (Eq. (logit)):    */
 /* dp_k/dtheta = p_k (-C_k + sum_{k' in od} p_k' C_k').                      */
@@ -504,9 +545,9 @@ double or_loss_grad_day(const or_day *d, const float *counts, const uint8_t *mas
                 int32_t od = n->rod[k];
                 double mean_c = 0.0;
                 for (int32_t k2 = 0; k2 < n->P; ++k2)
-                    if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->C[(size_t)h * n->P + k2];
+                    if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->Cc[(size_t)h * n->P + k2];
                 double pk = d->p[(size_t)h * n->P + k];
-                double dp = pk * (-d->C[(size_t)h * n->P + k] + mean_c);
+                double dp = pk * (-d->Cc[(size_t)h * n->P + k] + mean_c);
                 const double term = 2.0 * q[(size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * dp;
                 acc += term;
                 acc_abs += fabs(term);
@@ -537,9 +578,9 @@ void or_day_dense_B(const or_day *d, double *Bd) {
 /* Returns 0, or the first error code met.                                   */
 /* ------------------------------------------------------------------------ */
 int or_solve_days(const or_net *n, int32_t D, const int32_t *day_ids, const float *speeds,
-                  const float *counts, const uint8_t *mask, double theta, int32_t iters, double eta,
-                  double eps, int32_t row_chunk, uint64_t seed, int32_t n_threads, double *q_inout,
-                  double *G_inout, double *loss_out) {
+                  const float *counts, const uint8_t *mask, double theta, const double *choice_times,
+                  int32_t iters, double eta, double eps, int32_t row_chunk, uint64_t seed, int32_t n_threads,
+                  double *q_inout, double *G_inout, double *loss_out) {
     int status = OR_OK;
     size_t sA = (size_t)n->N * n->A, sO = (size_t)n->N * n->O, sK = (size_t)n->N * n->K;
     (void)n_threads;
@@ -556,6 +597,7 @@ int or_solve_days(const or_net *n, int32_t D, const int32_t *day_ids, const floa
             { if (status == OR_OK) status = err; }
             continue;
         }
+        if (choice_times) or_day_set_choice_times(d, choice_times + (size_t)n->N * n->P * i);
         loss_out[i] = or_solve_day(d, counts + sO * i, mask + sO * i, iters, eta, eps, row_chunk, seed,
                                    day_ids ? day_ids[i] : i, q_inout + sK * i, G_inout + sK * i, NULL);
         or_day_destroy(d);

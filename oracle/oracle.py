@@ -58,15 +58,18 @@ def lib():
                                    ct.c_int32, ct.c_uint64, ct.c_int32, _f64p, _f64p, _f64p]
         L.or_loss_grad_day.restype = ct.c_double
         L.or_loss_grad_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p, _f64p, _f64p, _f64p]
+        L.or_r2_day.restype = ct.c_double
+        L.or_r2_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p]
         L.or_splitmix64_next.restype = ct.c_uint64
         L.or_splitmix64_next.argtypes = [ct.POINTER(ct.c_uint64)]
         L.or_splitmix64_at.restype = ct.c_uint64
         L.or_splitmix64_at.argtypes = [ct.c_uint64, ct.c_uint64]
         L.or_permute_rows.argtypes = [_i32p, ct.c_int32, ct.c_uint64, ct.c_int32, ct.c_int32]
         L.or_solve_days.restype = ct.c_int
-        L.or_solve_days.argtypes = [ct.c_void_p, ct.c_int32, _i32p, _f32p, _f32p, _u8p, ct.c_double,
+        L.or_solve_days.argtypes = [ct.c_void_p, ct.c_int32, _i32p, _f32p, _f32p, _u8p, ct.c_double, _f64p,
                                     ct.c_int32, ct.c_double, ct.c_double, ct.c_int32, ct.c_uint64,
                                     ct.c_int32, _f64p, _f64p, _f64p]
+        L.or_day_set_choice_times.argtypes = [ct.c_void_p, _f64p]
         L.or_forward_days.restype = ct.c_int
         L.or_forward_days.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, ct.c_int32,
                                       _f64p]
@@ -121,15 +124,19 @@ class Net:
 
     # ---- multi-day drivers -------------------------------------------
     def solve_days(self, speeds, counts, mask, theta=0.1, iters=200, eta=5.0, eps=1e-10, row_chunk=0,
-                   seed=0, day_ids=None, q0=None, G0=None, n_threads=1):
+                   seed=0, day_ids=None, q0=None, G0=None, n_threads=1, choice_times=None):
+        """choice_times [D][N][P]: travel times of each day's route choice (a
+        traffic pattern's mean, see pattern_choice_times); None = own times."""
         D = speeds.shape[0]
         sp, ct_, mk = _c(speeds, np.float32), _c(counts, np.float32), _c(mask, np.uint8)
         q = np.zeros((D, self.N, self.K)) if q0 is None else _c(q0, np.float64).copy()
         G = np.zeros((D, self.N, self.K)) if G0 is None else _c(G0, np.float64).copy()
         loss = np.zeros(D)
         ids = None if day_ids is None else _c(day_ids, np.int32)
+        cc = None if choice_times is None else _c(choice_times, np.float64)
         rc = lib().or_solve_days(self.h, D, None if ids is None else _p(ids, _i32p), _p(sp, _f32p),
-                                 _p(ct_, _f32p), _p(mk, _u8p), theta, iters, eta, eps, row_chunk,
+                                 _p(ct_, _f32p), _p(mk, _u8p), theta, None if cc is None else _p(cc, _f64p),
+                                 iters, eta, eps, row_chunk,
                                  ct.c_uint64(seed), n_threads, _p(q, _f64p), _p(G, _f64p), _p(loss, _f64p))
         if rc != 0:
             raise OracleError(f"or_solve_days rc={rc}")
@@ -164,6 +171,14 @@ class Day:
 
     def set_theta(self, theta: float) -> None:
         lib().or_day_set_theta(self.h, theta)
+
+    def set_choice_times(self, Cc) -> None:
+        """Route choice from travel times Cc [N][P] (minutes), None = own."""
+        if Cc is None:
+            lib().or_day_set_choice_times(self.h, None)
+        else:
+            cc = _c(Cc, np.float64)
+            lib().or_day_set_choice_times(self.h, _p(cc, _f64p))
 
     @property
     def n_repairs(self) -> int:
@@ -248,6 +263,11 @@ class Day:
                                   None if tr is None else _p(tr, _f64p))
         return (q, G, loss, tr[:iters]) if trace else (q, G, loss)
 
+    def r2(self, counts, mask, q) -> float:
+        """R^2 of the link counts implied by q against the observed counts."""
+        cc, mm, qq = _c(counts, np.float32), _c(mask, np.uint8), _c(q, np.float64)
+        return float(lib().or_r2_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p)))
+
     def loss_grad(self, counts, mask, q, with_scale=False):
         """(loss, dL/dq, dL/dtheta) -- and, with ``with_scale``, the sum of the
         absolute values of the dL/dtheta terms (the scale of its rounding error)."""
@@ -259,6 +279,44 @@ class Day:
         loss = lib().or_loss_grad_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p), _p(dq, _f64p),
                                       ct.byref(dth), ct.byref(dabs))
         return (loss, dq, dth.value, dabs.value) if with_scale else (loss, dq, dth.value)
+
+
+def pattern_choice_times(net: "Net", speeds: np.ndarray, pattern) -> np.ndarray:
+    """Travel times of each day's route choice under traffic patterns (Eq.
+    (logit)): the mean, over the days of the day's pattern, of the route times
+    C [N][P] (Eq. (cost)); a day with pattern -1 keeps its own.  [D][N][P]."""
+    D = speeds.shape[0]
+    C = np.stack([net.day(speeds[d]).route_choice()[0] for d in range(D)])
+    out = C.copy()
+    pattern = np.asarray(pattern)
+    for c in set(pattern.tolist()) - {-1}:
+        days = np.flatnonzero(pattern == c)
+        out[days] = C[days].mean(axis=0)
+    return out
+
+
+def dar_distance(net: "Net", speeds: np.ndarray):
+    """Stability of the DAR across days (Sec. 5): each day's l2 distance between
+    its DAR matrix (Eq. (dar): rho for every route, link position, departure
+    interval h1 and arrival interval h2 < N) and the mean DAR over the given
+    days; also ||mean||^2.  FP64, entries keyed by (k, j, h1, h2)."""
+    D = speeds.shape[0]
+    keys, vals = [], []
+    for d in range(D):
+        kjh, rho = net.day(speeds[d]).dar()
+        kjh = kjh.astype(np.int64)
+        keys.append(((kjh[:, 0] * 64 + kjh[:, 1]) * net.N + kjh[:, 2]) * net.N + kjh[:, 3])
+        vals.append(rho)
+    uniq, inv = np.unique(np.concatenate(keys), return_inverse=True)
+    mean = np.bincount(inv, weights=np.concatenate(vals), minlength=uniq.size) / D
+    dist = np.empty(D)
+    start = 0
+    for d in range(D):
+        n = keys[d].size
+        rho_d = np.bincount(inv[start:start + n], weights=vals[d], minlength=uniq.size)
+        dist[d] = np.sqrt(((rho_d - mean) ** 2).sum())
+        start += n
+    return dist, float((mean ** 2).sum())
 
 
 def splitmix64(seed: int, n: int) -> list:

@@ -52,6 +52,9 @@ struct dode_ctx {
     float *d_counts = nullptr;
     uint32_t *d_mask = nullptr, *d_colact = nullptr;
     float *d_C = nullptr;
+    // traffic patterns (Eq. (logit) on a pattern's mean travel times)
+    float *d_Ceff = nullptr;                           // [D][P][Np] travel times of the route choice
+    bool patterns = false;
     int32_t *d_maxoff = nullptr;
     unsigned long long *d_repairs = nullptr;
     int64_t *d_tab_off = nullptr;
@@ -111,6 +114,9 @@ struct dode_ctx {
 namespace {
 
 void drop_graph(dode_ctx *ctx);
+
+// Travel times the route choice uses: each day's own, or its pattern's mean.
+const float *choice_C(const dode_ctx *ctx) { return ctx->patterns ? ctx->d_Ceff : ctx->d_C; }
 
 int fail(dode_ctx *c, int code, const std::string &msg) {
     if (c) c->err = msg;
@@ -513,7 +519,7 @@ FusedParams base_params(dode_ctx *ctx) {
     p.counts = ctx->d_counts;
     p.mask = ctx->d_mask;
     p.colact = ctx->d_colact;
-    p.C = ctx->d_C;
+    p.C = choice_C(ctx);
     p.maxoff = ctx->d_maxoff;
     p.tab_off = ctx->d_tab_off;
     p.traj_tab = ctx->d_traj_tab;
@@ -540,7 +546,7 @@ int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
     rc = ensure_slots(ctx, s, precision);
     if (rc) return rc;
     slot_params(ctx, s, &p);
-    CUL(launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, ctx->D, ctx->P, ctx->N,
+    CUL(launch_route_choice(choice_C(ctx), ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, ctx->D, ctx->P, ctx->N,
                             ctx->Np, ctx->d_pt, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -572,6 +578,8 @@ void free_days(dode_ctx *ctx) {
     dfree(ctx->d_mask);
     dfree(ctx->d_colact);
     dfree(ctx->d_C);
+    dfree(ctx->d_Ceff);
+    ctx->patterns = false;
     dfree(ctx->d_pt);
     dfree(ctx->d_maxoff);
     dfree(ctx->d_repairs);
@@ -619,7 +627,7 @@ int plain_prepare(dode_ctx *ctx, float theta, PlainParams *pp) {
     p.ticks = ctx->d_ticks;
     p.tab_off = ctx->d_tab_off;
     p.traj_tab = ctx->d_traj_tab;
-    p.C = ctx->d_C;
+    p.C = choice_C(ctx);
     p.theta = theta;
     p.n_days = ctx->D;
     p.err = ctx->d_err;
@@ -677,7 +685,7 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
         if (prec == DODE_PREC_BF16 && e == cudaSuccess)
             e = launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, gs);
         if (e == cudaSuccess)
-            e = launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, D, ctx->P,
+            e = launch_route_choice(choice_C(ctx), ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, D, ctx->P,
                                     ctx->N, ctx->Np, ctx->d_pt, gs);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), gs);
         // external event-record nodes: the events complete with each replay, so
@@ -1004,6 +1012,7 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
     }
     ctx->plain_ready = false;
     ctx->trace_iters = -1;
+    ctx->patterns = false;
     // speeds -> ticks (staged through the device when on the host)
     const size_t sp_bytes = (size_t)D * N * A * sizeof(float);
     const size_t ct_bytes = (size_t)D * N * O * sizeof(float);
@@ -1281,6 +1290,120 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
     return DODE_OK;
 }
 
+int dode_set_patterns(dode_ctx *ctx, const int32_t *pattern) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    drop_graph(ctx);
+    if (!pattern) {
+        ctx->patterns = false;
+        return DODE_OK;
+    }
+    const int D = ctx->D;
+    // groups of days sharing a pattern, in ascending day order; a day with
+    // label -1 is a group of its own
+    std::vector<int> order(D);
+    for (int d = 0; d < D; ++d) {
+        if (pattern[d] < -1) return fail(ctx, DODE_ERR_ARG, "pattern labels must be >= -1");
+        order[d] = d;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const long long ka = pattern[a] < 0 ? (1LL << 40) + a : pattern[a];
+        const long long kb = pattern[b] < 0 ? (1LL << 40) + b : pattern[b];
+        return ka < kb;
+    });
+    std::vector<int32_t> gptr(1, 0), gday(order.begin(), order.end());
+    for (int i = 1; i <= D; ++i)
+        if (i == D || pattern[order[i]] < 0 || pattern[order[i]] != pattern[order[i - 1]]) gptr.push_back(i);
+    if (!ctx->d_Ceff) CU(dalloc(&ctx->d_Ceff, (size_t)D * ctx->P * ctx->Np));
+    int32_t *dbuf = nullptr;
+    CU(dalloc(&dbuf, gptr.size() + gday.size()));
+    cudaError_t e = cudaMemcpyAsync(dbuf, gptr.data(), gptr.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dbuf + gptr.size(), gday.data(), gday.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess)
+        e = launch_pattern_times(ctx->d_C, (int)gptr.size() - 1, dbuf, dbuf + gptr.size(), ctx->P, ctx->N, ctx->Np,
+                                 ctx->d_Ceff, ctx->stream);
+    if (e == cudaSuccess) {
+        ++ctx->total_launches;
+        e = cudaStreamSynchronize(ctx->stream);
+    }
+    cudaFree(dbuf);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, DODE_ERR_CUDA, std::string("set_patterns: ") + cudaGetErrorString(e));
+    }
+    ctx->patterns = true;
+    return DODE_OK;
+}
+
+int dode_r2(dode_ctx *ctx, const float *q, float theta, double *r2, int32_t ptr_kind) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!q || !r2 || bad_ptr_kind(ptr_kind) || !std::isfinite(theta)) return fail(ctx, DODE_ERR_ARG, "r2 arguments");
+    int rc = fused_eval(ctx, MODE_LOSS, q, theta, ptr_kind);
+    if (rc) return rc;
+    double *dbuf = nullptr;
+    CU(dalloc(&dbuf, (size_t)ctx->D * 2));
+    cudaError_t e = launch_r2(ctx->d_counts, ctx->d_mask, ctx->D, ctx->O, ctx->N, ctx->Np, ctx->Nw, ctx->d_loss, dbuf,
+                              dbuf + ctx->D, ctx->stream);
+    if (e == cudaSuccess) {
+        ctx->total_launches += 2;
+        e = cudaMemcpyAsync(r2, dbuf + ctx->D, ctx->D * sizeof(double),
+                            ptr_kind == DODE_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dbuf);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, DODE_ERR_CUDA, std::string("r2: ") + cudaGetErrorString(e));
+    }
+    return DODE_OK;
+}
+
+int dode_dar_distance(dode_ctx *ctx, double *dist, double *mean_sq) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (!dist) return fail(ctx, DODE_ERR_ARG, "dar_distance arguments");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    DarParams p{};
+    p.N = ctx->N;
+    p.Np = ctx->Np;
+    p.A = ctx->A;
+    p.P = ctx->P;
+    p.L = ctx->L;
+    p.W = ctx->maxoff_max + 2;
+    p.n_days = ctx->D;
+    p.div = ctx->div;
+    p.rptr = ctx->d_rptr;
+    p.rlinks = ctx->d_rlinks;
+    p.ticks = ctx->d_ticks;
+    p.tab_off = ctx->d_tab_off;
+    p.traj_tab = ctx->d_traj_tab;
+    const int n_part = 4 * ctx->n_sm;
+    double *buf = nullptr;
+    const size_t nbar = (size_t)p.L * p.N * p.W;
+    CU(dalloc(&buf, nbar + n_part + 1 + ctx->D));
+    p.rbar = buf;
+    double *part = buf + nbar, *sq = part + n_part, *dd = sq + 1;
+    cudaError_t e = launch_dar_distance(p, part, n_part, sq, dd, ctx->stream);
+    if (e == cudaSuccess) {
+        ctx->total_launches += 4;
+        e = cudaMemcpyAsync(dist, dd, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    }
+    if (e == cudaSuccess && mean_sq) e = cudaMemcpyAsync(mean_sq, sq, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(ctx, DODE_ERR_CUDA, std::string("dar_distance: ") + cudaGetErrorString(e));
+    }
+    return DODE_OK;
+}
+
 int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, float *dq, double *dtheta,
                    int32_t ptr_kind) {
     if (!ctx) return DODE_ERR_ARG;
@@ -1503,7 +1626,7 @@ extern "C" int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float the
     __nv_bfloat16 *qb = reinterpret_cast<__nv_bfloat16 *>(base + off_qb);
     if (prec == DODE_PREC_BF16) CUL(launch_to_bf16(qi, qb, qn, ctx->stream));
     float *pt = reinterpret_cast<float *>(base + off_pt);
-    CUL(launch_route_choice(ctx->d_C, ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, theta, ctx->D, ctx->P, ctx->N,
+    CUL(launch_route_choice(choice_C(ctx), ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, theta, ctx->D, ctx->P, ctx->N,
                             ctx->Np, pt, ctx->stream));
     FusedParams p = base_params(ctx);
     p.mode = MODE_LOSS;

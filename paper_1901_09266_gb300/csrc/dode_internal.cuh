@@ -150,6 +150,18 @@ struct PlainParams {
     int *err;
 };
 
+// DAR stability check (quality.cu): mean DAR over the loaded days, held as
+// rbar[(l * N + h1) * W + (h2 - h1)] for route position l, and distances.
+struct DarParams {
+    int N, Np, A, P, L, W, n_days;
+    IntervalDiv div;
+    const int32_t *rptr, *rlinks;
+    const int32_t *ticks;      // [D][A][Np]
+    const int64_t *tab_off;    // [D] repaired trajectory table offset, -1 if none
+    const int32_t *traj_tab;
+    double *rbar;              // [L][N][W]
+};
+
 // error codes mirrored from dode.h for device use
 constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrUnsupported = -10;
 
@@ -177,6 +189,12 @@ cudaError_t launch_fused(const FusedParams &p, int precision, int grid, int bloc
                          cudaStream_t s);
 cudaError_t fused_occupancy(int precision, int block, size_t smem, int *blocks_per_sm);
 cudaError_t fused_set_attr(bool smem_ring, bool smem_ticks, int precision, size_t smem);
+cudaError_t launch_r2(const float *counts, const uint32_t *mask, int D, int O, int N, int Np, int Nw,
+                      const double *loss, double *sstot, double *r2, cudaStream_t s);
+cudaError_t launch_pattern_times(const float *C, int n_groups, const int32_t *gptr, const int32_t *gday, int P, int N,
+                                 int Np, float *Ceff, cudaStream_t s);
+cudaError_t launch_dar_distance(const DarParams &p, double *part, int n_part, double *rbar_sq, double *dist,
+                                cudaStream_t s);
 cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);

@@ -282,4 +282,92 @@ cudaError_t launch_route_choice(const float *C, const int32_t *rod, const int32_
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Goodness of fit (Step 6 of the framework, Sec. 4): per-day total sum of
+// squares of the observed counts about their masked mean, two passes in FP64
+// (block per day), and R^2 = 1 - SS_res / SS_tot from the day's masked loss.
+// ---------------------------------------------------------------------------
+__device__ double block_sum_d(double v, double *red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w];      // same order in every thread
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_sstot(const float *__restrict__ counts, const uint32_t *__restrict__ mask,
+                                               int O, int N, int Np, int Nw, double *__restrict__ sstot) {
+    __shared__ double red[8];
+    const int d = blockIdx.x;
+    const float *c = counts + (size_t)d * O * Np;
+    const uint32_t *m = mask + (size_t)d * O * Nw;
+    double s = 0.0, n = 0.0;
+    for (int i = threadIdx.x; i < O * N; i += blockDim.x) {
+        const int o = i / N, h = i - o * N;
+        if ((m[(size_t)o * Nw + (h >> 5)] >> (h & 31)) & 1u) {
+            s += c[(size_t)o * Np + h];
+            n += 1.0;
+        }
+    }
+    s = block_sum_d(s, red);
+    n = block_sum_d(n, red);
+    const double mean = n > 0.0 ? s / n : 0.0;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < O * N; i += blockDim.x) {
+        const int o = i / N, h = i - o * N;
+        if ((m[(size_t)o * Nw + (h >> 5)] >> (h & 31)) & 1u) {
+            const double e = (double)c[(size_t)o * Np + h] - mean;
+            ss += e * e;
+        }
+    }
+    ss = block_sum_d(ss, red);
+    if (threadIdx.x == 0) sstot[d] = ss;
+}
+
+__global__ void k_r2(const double *__restrict__ loss, const double *__restrict__ sstot, int D, double *__restrict__ r2) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < D) r2[d] = sstot[d] > 0.0 ? 1.0 - loss[d] / sstot[d] : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+cudaError_t launch_r2(const float *counts, const uint32_t *mask, int D, int O, int N, int Np, int Nw,
+                      const double *loss, double *sstot, double *r2, cudaStream_t s) {
+    k_sstot<<<D, 256, 0, s>>>(counts, mask, O, N, Np, Nw, sstot);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_r2<<<(D + 127) / 128, 128, 0, s>>>(loss, sstot, D, r2);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Pattern-level route choice (Eq. (logit) takes the mean travel time of each
+// path over the days of a traffic pattern): Ceff[d] = mean over the days of
+// d's group of C[d'], FP64 sums in ascending day order.  One thread per
+// (group, route, interval).
+// ---------------------------------------------------------------------------
+__global__ void k_pattern_times(const float *__restrict__ C, int n_groups, const int32_t *__restrict__ gptr,
+                                const int32_t *__restrict__ gday, int P, int N, int Np, float *__restrict__ Ceff) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)n_groups * P * N) return;
+    const int g = (int)(i / ((long long)P * N));
+    const int rest = (int)(i - (long long)g * P * N);
+    const int k = rest / N, h = rest - k * N;
+    const int d0 = gptr[g], d1 = gptr[g + 1];
+    double s = 0.0;
+    for (int x = d0; x < d1; ++x) s += (double)C[((size_t)gday[x] * P + k) * Np + h];
+    const float m = (float)(s / (double)(d1 - d0));
+    for (int x = d0; x < d1; ++x) Ceff[((size_t)gday[x] * P + k) * Np + h] = m;
+}
+
+cudaError_t launch_pattern_times(const float *C, int n_groups, const int32_t *gptr, const int32_t *gday, int P, int N,
+                                 int Np, float *Ceff, cudaStream_t s) {
+    const long long n = (long long)n_groups * P * N;
+    if (n == 0) return cudaSuccess;
+    k_pattern_times<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(C, n_groups, gptr, gday, P, N, Np, Ceff);
+    return cudaGetLastError();
+}
+
 }  // namespace dode

@@ -30,7 +30,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 # every entry point of include/dode.h
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
-           "dode_loss_grad", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
+           "dode_loss_grad", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
            "dode_last_kernel_ms", "dode_last_launches", "dode_total_launches", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
@@ -86,6 +86,9 @@ def load(path: str = LIB_PATH):
         "dode_forward": (ct.c_int, [vp, vp, vp, i32]),
         "dode_loss": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_loss_grad": (ct.c_int, [vp, vp, f32, vp, vp, vp, i32]),
+        "dode_set_patterns": (ct.c_int, [vp, vp]),
+        "dode_r2": (ct.c_int, [vp, vp, f32, vp, i32]),
+        "dode_dar_distance": (ct.c_int, [vp, vp, vp]),
         "dode_loss_static_scratch": (ct.c_int, [vp, vp, f32, vp]),
         "dode_get_ticks": (ct.c_int, [vp, i32, vp]),
         "dode_get_route_times": (ct.c_int, [vp, i32, vp]),
@@ -268,6 +271,36 @@ class Context:
         th = self.opt.theta_per_min if theta is None else theta
         self._check(load().dode_loss_grad(self.h, pq, th, loss.ctypes.data, pd, dth.ctypes.data, kind))
         return loss, dq, dth
+
+    def set_patterns(self, pattern=None) -> None:
+        """Traffic pattern label of each loaded day (-1 = own travel times);
+        None clears them.  Route choice then uses each pattern's mean times."""
+        if pattern is None:
+            self._check(load().dode_set_patterns(self.h, None))
+            return
+        lab = np.ascontiguousarray(pattern, dtype=np.int32)
+        if lab.shape != (self.D,):
+            raise ValueError(f"pattern must have shape ({self.D},)")
+        self._check(load().dode_set_patterns(self.h, lab.ctypes.data))
+
+    def r2(self, q, theta: Optional[float] = None, r2_out=None):
+        """Per-day R^2 of the link counts implied by ``q`` against the observed
+        counts (Step 6 quality check); NaN where a day has SS_tot = 0."""
+        pq, _, kq = self._ptr(q, np.float32, (self.D, self.N, self.K))
+        out = np.empty(self.D, np.float64) if r2_out is None else r2_out
+        pr, _, kr = self._ptr(out, np.float64, (self.D,))
+        kind = self._same_kind((kq, True), (kr, True))
+        th = self.opt.theta_per_min if theta is None else theta
+        self._check(load().dode_r2(self.h, pq, th, pr, kind))
+        return out
+
+    def dar_distance(self):
+        """(dist [D], ||mean DAR||^2): each loaded day's DAR l2 distance from
+        the mean DAR over the loaded days."""
+        dist = np.empty(self.D, np.float64)
+        sq = np.zeros(1, np.float64)
+        self._check(load().dode_dar_distance(self.h, dist.ctypes.data, sq.ctypes.data))
+        return dist, float(sq[0])
 
     def loss_static_scratch(self, q, loss_out, theta: Optional[float] = None) -> None:
         """Per-day loss into ``loss_out`` without any device allocation (see

@@ -436,3 +436,114 @@ def test_permutation_is_uniform():
     assert chi2 < 20.5          # 5 dof, p ~ 0.001
     big = orc.permute_rows(np.arange(1000), seed=5, day=3, epoch=2)
     assert sorted(big.tolist()) == list(range(1000))
+
+
+# ---------------------------------------------------------------------------
+# quality check (Step 6): R^2 of the fitted link counts
+# ---------------------------------------------------------------------------
+
+def test_r2_pins():
+    w, day, q_true, counts = _tiny_instance(noise=0.0)
+    mask = np.ones_like(counts, np.uint8)
+    # counts produced by q itself (up to their FP32 rounding): a perfect fit
+    assert day.r2(counts, mask, q_true) > 1.0 - 1e-10
+    # scaling counts and demand by a power of two changes no ratio
+    w2, day2, q2, counts2 = _tiny_instance(noise=0.05)
+    m2 = np.ones_like(counts2, np.uint8)
+    m2[1, 0] = 0
+    qa = q2 * 0.8
+    assert day2.r2(4 * counts2, m2, 4 * qa) == pytest.approx(day2.r2(counts2, m2, qa), rel=1e-12)
+    # against the dense assignment matrix of Eq. (assign)
+    Bd = day2.dense_B()
+    xhat = (Bd @ qa.reshape(-1)).reshape(counts2.shape)
+    obs = m2.astype(bool)
+    x = counts2.astype(np.float64)
+    want = 1.0 - ((xhat - x)[obs] ** 2).sum() / ((x[obs] - x[obs].mean()) ** 2).sum()
+    assert day2.r2(counts2, m2, qa) == pytest.approx(want, rel=1e-12)
+    # R^2 < 1 for an imperfect fit; undefined (NaN) for constant observed counts
+    assert day2.r2(counts2, m2, qa) < 1.0
+    assert np.isnan(day2.r2(np.full_like(counts2, 7.0), m2, qa))
+    assert np.isnan(day2.r2(counts2, np.zeros_like(m2), qa))
+
+
+def test_dar_distance_pins():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    sp = w.speeds([0, 1, 2])
+    # identical days: every day is the mean
+    same = np.stack([sp[0], sp[0], sp[0]])
+    dist, _ = orc.dar_distance(net, same)
+    assert np.all(dist < 1e-12)             # (3 rho) / 3 up to rounding
+    # one day differs from D - 1 identical days: closed forms over ||rho_b - rho_a||
+    D = 4
+    mix = np.stack([sp[0]] * (D - 1) + [sp[1]])
+    dist, msq = orc.dar_distance(net, mix)
+    ra = {tuple(k): v for k, v in zip(*[x.tolist() for x in net.day(sp[0]).dar()])}
+    rb = {tuple(k): v for k, v in zip(*[x.tolist() for x in net.day(sp[1]).dar()])}
+    keys = set(ra) | set(rb)
+    diff = np.sqrt(sum((rb.get(k, 0.0) - ra.get(k, 0.0)) ** 2 for k in keys))
+    assert diff > 0
+    np.testing.assert_allclose(dist[:D - 1], diff / D, rtol=1e-12)
+    assert dist[D - 1] == pytest.approx((D - 1) * diff / D, rel=1e-12)
+    mean = {k: ((D - 1) * ra.get(k, 0.0) + rb.get(k, 0.0)) / D for k in keys}
+    assert msq == pytest.approx(sum(v * v for v in mean.values()), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# pattern-level route choice (Eq. (logit) on a pattern's mean travel times)
+# ---------------------------------------------------------------------------
+
+def test_pattern_route_choice_pins():
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    sp = w.speeds([0, 1, 2])
+    Cc = orc.pattern_choice_times(net, sp, [0, 0, -1])
+    C0, p0 = net.day(sp[0]).route_choice()
+    C1, _ = net.day(sp[1]).route_choice()
+    C2, p2 = net.day(sp[2]).route_choice()
+    np.testing.assert_array_equal(Cc[2], C2)                 # pattern -1: own times
+    np.testing.assert_allclose(Cc[0], 0.5 * (C0 + C1), rtol=1e-15)
+    # a one-day pattern is the day's own route choice
+    d = net.day(sp[2])
+    d.set_choice_times(orc.pattern_choice_times(net, sp[2:3], [4])[0])
+    np.testing.assert_allclose(d.route_choice()[1], p2, rtol=1e-15)
+    # two-route ODs: p_1 = 1 / (1 + exp(-theta (c~_2 - c~_1))) on the mean times
+    d = net.day(sp[0], theta=0.1)
+    d.set_choice_times(Cc[0])
+    _, p = d.route_choice()
+    rod = np.asarray(w.routes.route_od)
+    two = [od for od in range(w.routes.n_od) if (rod == od).sum() == 2]
+    assert two
+    for od in two:
+        k1, k2 = np.flatnonzero(rod == od)
+        want = 1.0 / (1.0 + np.exp(-0.1 * (Cc[0][:, k2] - Cc[0][:, k1])))
+        np.testing.assert_allclose(p[:, k1], want, rtol=1e-12)
+    # theta = 0: uniform split whatever the times
+    d.set_theta(0.0)
+    _, p = d.route_choice()
+    for od in two:
+        np.testing.assert_allclose(p[:, np.flatnonzero(rod == od)], 0.5, rtol=1e-15)
+
+
+def test_pattern_dtheta_matches_finite_differences():
+    # dL/dtheta differentiates the route choice on the pattern's times
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    sp = w.speeds([0, 1])
+    Cc = orc.pattern_choice_times(net, sp, [0, 0])
+    counts = w.counts_from(net.forward_days(sp, w.q_true([0, 1]).astype(np.float64)), [0, 1])
+    mask = np.ones_like(counts[0], np.uint8)
+    q = w.q_true([0])[0].astype(np.float64) * 0.9
+
+    def loss_at(theta):
+        d = net.day(sp[0], theta=theta)
+        d.set_choice_times(Cc[0])
+        return d.loss_grad(counts[0], mask, q)[0]
+
+    d = net.day(sp[0], theta=0.1)
+    d.set_choice_times(Cc[0])
+    _, _, dth = d.loss_grad(counts[0], mask, q)
+    h = 1e-3
+    d1 = (loss_at(0.1 + h) - loss_at(0.1 - h)) / (2 * h)
+    d2 = (loss_at(0.1 + h / 2) - loss_at(0.1 - h / 2)) / h
+    assert dth == pytest.approx((4 * d2 - d1) / 3, rel=1e-6)
