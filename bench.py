@@ -251,7 +251,7 @@ def run_reference(args):
 
 def run_gpu(args):
     import torch
-    from paper_1901_09266_gb300 import build, dode
+    from paper_1901_09266_gb300 import build, dode, synth
 
     world, rank, local = dist_env()
     if world > 1:
@@ -402,6 +402,57 @@ def run_gpu(args):
             v["speedup_vs_plain_fp32"] = v["day_iter_per_s"] / base["day_iter_per_s"]
             v["final_loss_rel_diff_vs_plain"] = abs(v["final_loss"] - base["final_loss"]) / base["final_loss"]
 
+    # next rows on the same days: pattern-level route choice (weekday / weekend /
+    # holiday labels), the R^2 quality check and the DAR distance to the mean DAR
+    nxt = None
+    if args.next_rows and rank == 0:
+        nxt = {}
+        c3 = dode.Context.from_workload(w, precision=prec)
+        c3.use_torch_stream()
+        c3.set_days(ct_d, sp_d, mk_d)
+        labels = np.array([synth.day_type(w, d) for d in days], np.int32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c3.set_patterns(labels)
+        torch.cuda.synchronize()
+        nxt["set_patterns_ms"] = (time.perf_counter() - t0) * 1e3
+        c3.solve(args.compare_epochs, args.step, args.batch, q_out=q_d, loss_out=l_d)
+        nxt["pattern_solve"] = {"day_iter_per_s": D * args.compare_epochs / (c3.last_kernel_ms() / 1e3),
+                                "epochs": args.compare_epochs, "patterns": int(len(set(labels.tolist())))}
+        r2_d = torch.empty(D, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c3.r2(q_d, r2_out=r2_d)
+        torch.cuda.synchronize()
+        r2 = r2_d.cpu().numpy()
+        nxt["r2"] = {"ms": (time.perf_counter() - t0) * 1e3, "mean": float(np.nanmean(r2)),
+                     "after_epochs": args.compare_epochs}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dist, msq = c3.dar_distance()
+        ms_d = (time.perf_counter() - t0) * 1e3
+        nxt["dar_distance"] = {"ms": ms_d, "days": D, "mean_dist": float(dist.mean()),
+                               "rel_to_mean_norm": float(dist.mean() / np.sqrt(msq))}
+        c3.close()
+        # the paper's efficiency experiment at its largest size: dense random
+        # n x n NNLS by Algorithm 1; the two products read B (4 n^2 bytes) once each
+        n = args.dense_n
+        rng = np.random.default_rng(1901)
+        Bh = (rng.standard_normal((n, n), dtype=np.float32) / np.float32(np.sqrt(n)))
+        xt = np.abs(rng.standard_normal((n, 1))).astype(np.float32)
+        Bd = torch.from_numpy(Bh).to(dev)
+        Yd = Bd @ torch.from_numpy(xt).to(dev)
+        dode.dense_nnls(Bd, Yd, 3, 0.05)                                   # warm-up
+        _, _, ld, ms_dense = dode.dense_nnls(Bd, Yd, args.dense_iters, 0.05)
+        per = ms_dense / (args.dense_iters + 0.5)                         # + the final residual pass
+        nxt["dense_nnls"] = {"n": n, "m": 1, "iters": args.dense_iters, "ms_per_iter": per,
+                             "roofline": {"bound": "hbm", "achieved": 8.0 * n * n / (per / 1e3) / 1e9,
+                                          "peak": peaks.get("hbm_gbs") or 6800.0, "unit": "GB/s",
+                                          "frac": 8.0 * n * n / (per / 1e3) / 1e9 / (peaks.get("hbm_gbs") or 6800.0),
+                                          "bytes_per_iter": 8 * n * n},
+                             "final_loss": float(ld.sum().item())}
+        del Bd, Yd
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -430,6 +481,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "clocks": clk,
             "forms": forms,
+            "next": nxt,
             "final_loss_total": final_loss,
         }
         print(json.dumps(line), flush=True)
@@ -460,6 +512,9 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="replay the solve as a CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with the autotuner")
     ap.add_argument("--compare-epochs", type=int, default=20)
+    ap.add_argument("--next-rows", type=int, default=1, help="time the pattern, R^2, DAR-distance and dense rows")
+    ap.add_argument("--dense-n", type=int, default=6000)
+    ap.add_argument("--dense-iters", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-days", type=int, default=128)
     ap.add_argument("--ref-epochs", type=int, default=20)

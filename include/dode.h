@@ -196,6 +196,29 @@ int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, flo
                    double *dtheta, int32_t ptr_kind);
 
 /*
+ * dode_dense_nnls -- the paper's efficiency experiment (Sec. 5, "Algorithm
+ * efficiency": a dense random B, y = B x with x >= 0, NNLS(B, y)) solved by
+ * Algorithm 1 with full-row updates, for m right-hand sides sharing B:
+ * per column j, r = B x_j - y_j, g = B^T r (no factor 2, as Algorithm 1
+ * prints it), G += g^2, x_j = max(x_j - step g / (sqrt(G) + eps), 0).
+ * Standalone: no context is needed.
+ *   B          [n_rows][n_cols] FP32, row-major
+ *   Y          [n_rows][m] FP32
+ *   X          [n_cols][m] FP32, in: the starting point, out: the iterate after `iters` steps
+ *   G          [n_cols][m] FP32 Adagrad accumulator in/out, or NULL to start from 0
+ *   loss       [m] FP64 out: ||B x_j - y_j||^2 of the final iterate
+ *   kernel_ms  out (may be NULL): GPU time of the iterations and the final residual
+ * All arrays are host or device pointers per ptr_kind; stream is a cudaStream_t
+ * (NULL = default stream); the call returns when its work is complete.
+ * Limits: 1 <= m <= 8 and n_cols * m <= 51200 (x is staged in shared memory).
+ * Errors: DODE_ERR_ARG, DODE_ERR_UNSUPPORTED (the limit), DODE_ERR_OOM, DODE_ERR_CUDA;
+ * the message goes to stderr.
+ */
+int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, const float *Y, int32_t iters,
+                    float step, float eps, float *X, float *G, double *loss, double *kernel_ms, int32_t ptr_kind,
+                    void *stream);
+
+/*
  * dode_set_patterns -- traffic patterns of the loaded days (Step 2-3 of the
  * framework, Sec. 4; Eq. (logit) computes a pattern's route choice from the
  * mean travel time of each path over the pattern's days).

@@ -38,6 +38,8 @@ struct dode_ctx {
     std::vector<int32_t> step_ods;                     // ODs of groups that do not own them
     int G = 0;
     int4 *d_groute = nullptr;
+    std::vector<int2> rtab;                            // [L] (link, (observed column + 1) | event word << 24)
+    int2 *d_rtab = nullptr;
     int32_t *d_gptr = nullptr, *d_task_grp = nullptr, *d_rev = nullptr;
     int32_t *d_god_ptr = nullptr, *d_god = nullptr, *d_godr_ptr = nullptr, *d_godr = nullptr, *d_step_ods = nullptr;
     float *d_pt = nullptr;                             // route choice table [D][P][Np]
@@ -251,6 +253,7 @@ int output_plain(dode_ctx *ctx, const void *src, void *dst, size_t bytes, int pt
 
 struct FusedShape {
     int block, grid, ring_rows, tick_rows, tiles_per_phase;
+    int rtab_off;          // byte offset of the route-position table in shared memory, -1 = read from global
     size_t smem;
 };
 
@@ -298,7 +301,14 @@ int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
         }
     }
     if (F == 0) F = ntiles;
-    const size_t smem = fused_smem_bytes(ctx, R, RW);
+    size_t smem = fused_smem_bytes(ctx, R, RW);
+    // the packed route-position table goes to shared memory when it fits beside the windows
+    const size_t rtab_bytes = align16((size_t)ctx->L * sizeof(int2));
+    s->rtab_off = -1;
+    if (align16(smem) + rtab_bytes <= budget) {
+        s->rtab_off = (int)align16(smem);
+        smem = align16(smem) + rtab_bytes;
+    }
     if (smem > budget + reserve)
         return fail(ctx, DODE_ERR_UNSUPPORTED, "route tables of this network do not fit in shared memory");
     int occ = 0;
@@ -362,6 +372,7 @@ void slot_params(const dode_ctx *ctx, const FusedShape &s, FusedParams *p) {
     p->ring_rows = s.ring_rows;
     p->tick_rows = s.tick_rows;
     p->tiles_per_phase = s.tiles_per_phase;
+    p->rtab_off = s.rtab_off;
     p->gp = ctx->d_gp;
     p->lab = ctx->d_lab;
     p->rc_bins = ctx->d_rc_bins;
@@ -462,6 +473,9 @@ void build_groups(dode_ctx *ctx, const int32_t *link_tail) {
     for (int x = 0; x < P; ++x)        // bit 8 of the start-depth word: the group owns the route's OD
         if (owner[ctx->rod[ctx->groute[x].x]] == gof[ctx->groute[x].x]) ctx->groute[x].w |= 1 << 8;
     for (int x = 0; x < P; ++x) ctx->groute[x].w |= ctx->rod[ctx->groute[x].x] << 9;   // bits 9..: the OD
+    ctx->rtab.resize(ctx->L);
+    for (int l = 0; l < ctx->L; ++l)
+        ctx->rtab[l] = make_int2(ctx->rlinks[l], (ctx->obs_col[ctx->rlinks[l]] + 1) | (ctx->rev[l] << 24));
     ctx->god_ptr.assign(1, 0);
     ctx->godr_ptr.assign(1, 0);
     for (int g = 0; g < ctx->G; ++g) {
@@ -502,6 +516,9 @@ FusedParams base_params(dode_ctx *ctx) {
     p.task_od = ctx->d_task_od;
     p.rpack = ctx->d_rpack;
     p.groute = ctx->d_groute;
+    p.rtab = ctx->d_rtab;
+    p.rtab_off = -1;
+    p.rptr_total = ctx->L;
     p.gptr = ctx->d_gptr;
     p.task_grp = ctx->d_task_grp;
     p.rev = ctx->d_rev;
@@ -903,6 +920,7 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     CUB(upload(&ctx->d_len, ctx->len, ctx->stream));
     CUB(upload(&ctx->d_rpack, ctx->rpack, ctx->stream));
     CUB(upload(&ctx->d_groute, ctx->groute, ctx->stream));
+    CUB(upload(&ctx->d_rtab, ctx->rtab, ctx->stream));
     CUB(upload(&ctx->d_gptr, ctx->gptr, ctx->stream));
     CUB(upload(&ctx->d_task_grp, ctx->task_grp, ctx->stream));
     CUB(upload(&ctx->d_rev, ctx->rev, ctx->stream));
@@ -942,6 +960,7 @@ void dode_destroy(dode_ctx *ctx) {
     dfree(ctx->d_len);
     dfree(ctx->d_rpack);
     dfree(ctx->d_groute);
+    dfree(ctx->d_rtab);
     dfree(ctx->d_gptr);
     dfree(ctx->d_task_grp);
     dfree(ctx->d_rev);
@@ -1287,6 +1306,93 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
     if (rc) return rc;
     CU(cudaMemcpyAsync(loss, ctx->d_loss, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, const float *Y, int32_t iters,
+                    float step, float eps, float *X, float *G, double *loss, double *kernel_ms, int32_t ptr_kind,
+                    void *stream) {
+    auto bail = [&](int code, const std::string &msg) {
+        fprintf(stderr, "dode_dense_nnls: %s\n", msg.c_str());
+        return code;
+    };
+    if (n_rows < 1 || n_cols < 1 || m < 1 || m > 8 || iters < 0 || !(step > 0.f) || !std::isfinite(step) ||
+        !(eps >= 0.f) || !B || !Y || !X || !loss || (ptr_kind != DODE_PTR_HOST && ptr_kind != DODE_PTR_DEVICE))
+        return bail(DODE_ERR_ARG, "arguments (1 <= m <= 8, iters >= 0, step > 0)");
+    if ((long long)n_cols * m * sizeof(float) > 200 * 1024)
+        return bail(DODE_ERR_UNSUPPORTED, "n_cols * m must be at most 51200 (x is staged in shared memory)");
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(DODE_ERR_CUDA, "no CUDA device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nB = (size_t)n_rows * n_cols, nY = (size_t)n_rows * m, nX = (size_t)n_cols * m;
+    DenseParams p{};
+    p.nr = n_rows;
+    p.nc = n_cols;
+    p.m = m;
+    p.eta = step;
+    p.eps = eps;
+    p.grid_r = (int)std::min<long long>(((long long)n_rows + 7) / 8, 4LL * n_sm);
+    // row blocks of 32 rows (8 rows per load batch); partial gradients per block
+    p.rows_per_cta = 32;
+    p.grid_g = (n_rows + p.rows_per_cta - 1) / p.rows_per_cta;
+    // one device allocation: (B, y when on the host) x, G, r, partials, loss
+    const bool host = ptr_kind == DODE_PTR_HOST;
+    const size_t f_count = (host ? nB + nY : 0) + nX + nX + nY + (size_t)p.grid_g * nX;
+    const size_t d_count = (size_t)p.grid_r * m + m;
+    char *buf = nullptr;
+    const size_t f_bytes = (f_count * sizeof(float) + 255) & ~(size_t)255;
+    if (cudaMalloc(&buf, f_bytes + d_count * sizeof(double)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bail(DODE_ERR_OOM, "device memory");
+    }
+    float *f = reinterpret_cast<float *>(buf);
+    p.B = host ? f : B;
+    if (host) f += nB;
+    p.y = host ? f : Y;
+    if (host) f += nY;
+    p.x = f;
+    f += nX;
+    p.G = f;
+    f += nX;
+    p.r = f;
+    f += nY;
+    p.gpart = f;
+    p.lpart = reinterpret_cast<double *>(buf + f_bytes);
+    double *dloss = p.lpart + (size_t)p.grid_r * m;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    if (host) e = cudaMemcpyAsync(const_cast<float *>(p.B), B, nB * sizeof(float), in, st);
+    if (e == cudaSuccess && host) e = cudaMemcpyAsync(const_cast<float *>(p.y), Y, nY * sizeof(float), in, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p.x, X, nX * sizeof(float), in, st);
+    if (e == cudaSuccess)
+        e = G ? cudaMemcpyAsync(p.G, G, nX * sizeof(float), in, st) : cudaMemsetAsync(p.G, 0, nX * sizeof(float), st);
+    if (e == cudaSuccess) e = dense_set_smem((size_t)n_cols * m * sizeof(float), (size_t)p.rows_per_cta * m * sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) e = dense_iteration(p, true, st);
+    if (e == cudaSuccess) e = dense_iteration(p, false, st);     // residual and loss of the final x
+    if (e == cudaSuccess) e = dense_loss(p, dloss, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    const cudaMemcpyKind out = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X, p.x, nX * sizeof(float), out, st);
+    if (e == cudaSuccess && G) e = cudaMemcpyAsync(G, p.G, nX * sizeof(float), out, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dloss, m * sizeof(double), host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess && kernel_ms) {
+        e = cudaEventElapsedTime(&ms, e0, e1);
+        *kernel_ms = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bail(DODE_ERR_CUDA, cudaGetErrorString(e));
+    }
     return DODE_OK;
 }
 
@@ -1642,6 +1748,7 @@ extern "C" int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float the
     p.ring_rows = sh.ring_rows;
     p.tick_rows = sh.tick_rows;
     p.tiles_per_phase = sh.tiles_per_phase;
+    p.rtab_off = sh.rtab_off;
     p.queue = reinterpret_cast<int *>(base);
     CUL(launch_fused(p, prec, grid, sh.block, sh.smem, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));

@@ -57,6 +57,7 @@ __device__ __forceinline__ int interval_of(int t, const IntervalDiv &d) {
 struct FusedParams {
     // sizes
     int N, Np, Nw, A, O, Ow, K, P;
+    int rptr_total;            // L, route positions over all routes
     IntervalDiv div;
     // network / routes (device)
     const int32_t *rptr;       // [P+1]
@@ -67,6 +68,8 @@ struct FusedParams {
     const int32_t *task_od;    // [K] OD processing order (largest work first)
     const int2 *rpack;         // [L] (link, observed column or -1) of every route position
     const int4 *groute;        // [P] walk order: (route, first position, links, start depth | own << 8 | OD << 9)
+    const int2 *rtab;          // [L] (link, (observed column + 1) | event word << 24) of every route position
+    int rtab_off;              // byte offset of its shared-memory copy, -1 = read it from global memory
     const int32_t *gptr;       // [G+1] routes of each walk group in groute
     const int32_t *task_grp;   // [G] group processing order (largest walk first)
     const int32_t *rev;        // [L] (E << 1) | save of every route position (see build_groups)
@@ -162,6 +165,15 @@ struct DarParams {
     double *rbar;              // [L][N][W]
 };
 
+// Dense NNLS by Algorithm 1 (dense.cu): B [nr][nc], y / r [nr][m], x / G [nc][m].
+struct DenseParams {
+    const float *B, *y;
+    float *x, *G, *r, *gpart;
+    double *lpart;
+    int nr, nc, m, grid_r, grid_g, rows_per_cta;
+    float eta, eps;
+};
+
 // error codes mirrored from dode.h for device use
 constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrUnsupported = -10;
 
@@ -195,6 +207,9 @@ cudaError_t launch_pattern_times(const float *C, int n_groups, const int32_t *gp
                                  int Np, float *Ceff, cudaStream_t s);
 cudaError_t launch_dar_distance(const DarParams &p, double *part, int n_part, double *rbar_sq, double *dist,
                                 cudaStream_t s);
+cudaError_t dense_iteration(const DenseParams &p, bool step, cudaStream_t s);
+cudaError_t dense_loss(const DenseParams &p, double *loss, cudaStream_t s);
+cudaError_t dense_set_smem(size_t resid_bytes, size_t grad_bytes);
 cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);

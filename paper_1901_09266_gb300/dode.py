@@ -30,7 +30,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 # every entry point of include/dode.h
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
-           "dode_loss_grad", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
+           "dode_loss_grad", "dode_dense_nnls", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
            "dode_last_kernel_ms", "dode_last_launches", "dode_total_launches", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
         "dode_forward": (ct.c_int, [vp, vp, vp, i32]),
         "dode_loss": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_loss_grad": (ct.c_int, [vp, vp, f32, vp, vp, vp, i32]),
+        "dode_dense_nnls": (ct.c_int, [i32, i32, i32, vp, vp, i32, f32, f32, vp, vp, vp, vp, i32, vp]),
         "dode_set_patterns": (ct.c_int, [vp, vp]),
         "dode_r2": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_dar_distance": (ct.c_int, [vp, vp, vp]),
@@ -349,3 +350,40 @@ class Context:
         self._check(load().dode_set_launch(self.h, block_threads, ctas_per_sm))
         self.opt.max_ctas = max_ctas
         self._check(load().dode_set_max_ctas(self.h, max_ctas))
+
+
+def dense_nnls(B, Y, iters: int, step: float, X0=None, G0=None, eps: float = 1e-10, stream=None):
+    """Algorithm 1 on a dense B for the columns of Y (dode_dense_nnls).
+
+    numpy arrays run from host memory; CUDA torch tensors in place on the
+    device.  Returns (X, G, loss, kernel_ms)."""
+    dev = _is_torch(B)
+    if dev:
+        import torch
+        nr, nc = B.shape
+        m = Y.shape[1]
+        X = torch.zeros((nc, m), dtype=torch.float32, device=B.device) if X0 is None else X0
+        G = torch.zeros((nc, m), dtype=torch.float32, device=B.device) if G0 is None else G0
+        loss = torch.empty(m, dtype=torch.float64, device=B.device)
+        args = [B.data_ptr(), Y.data_ptr(), X.data_ptr(), G.data_ptr(), loss.data_ptr()]
+        kind = PTR_DEVICE
+        st = ct.c_void_p(torch.cuda.current_stream().cuda_stream if stream is None else stream)
+    else:
+        B = _host(B, np.float32)
+        Y = _host(Y, np.float32)
+        nr, nc = B.shape
+        m = Y.shape[1]
+        X = np.zeros((nc, m), np.float32) if X0 is None else _host(X0, np.float32).copy()
+        G = np.zeros((nc, m), np.float32) if G0 is None else _host(G0, np.float32).copy()
+        loss = np.empty(m, np.float64)
+        args = [B.ctypes.data, Y.ctypes.data, X.ctypes.data, G.ctypes.data, loss.ctypes.data]
+        kind = PTR_HOST
+        st = ct.c_void_p(stream)
+    if Y.shape[0] != nr:
+        raise ValueError("B and Y must have the same number of rows")
+    ms = ct.c_double(0.0)
+    rc = load().dode_dense_nnls(int(nr), int(nc), int(m), args[0], args[1], int(iters), float(step), float(eps),
+                                args[2], args[3], args[4], ct.addressof(ms), kind, st)
+    if rc != OK:
+        raise DodeError(rc, "dode_dense_nnls failed (details on stderr)")
+    return X, G, loss, ms.value

@@ -235,6 +235,12 @@ def _day_type(w: Workload, d: int) -> int:
     return 1 if (d + 2) % 7 >= 5 else 0
 
 
+def day_type(w: Workload, d: int) -> int:
+    """The generator's day type of day d (0 weekday, 1 weekend, 2 holiday): a
+    stand-in for traffic-pattern labels that a clustering step would supply."""
+    return _day_type(w, d)
+
+
 def _day_speeds(w: Workload, d: int) -> np.ndarray:
     net = w.net
     N, A = w.n_intervals, net.n_links

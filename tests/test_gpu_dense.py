@@ -1,0 +1,57 @@
+"""Dense NNLS by Algorithm 1 on the GPU (the paper's efficiency experiment)
+against the FP64 oracle: aligned and ragged shapes, several right-hand sides,
+a warm start from a given iterate and accumulator, host and device pointers."""
+import numpy as np
+import pytest
+
+from oracle.dense_nnls import spgd_dense
+from paper_1901_09266_gb300 import dode
+from tests.helpers import rel_norm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1901_09266_gb300 import build
+    build.build()
+
+
+def _instance(nr, nc, m, seed):
+    rng = np.random.default_rng(seed)
+    B = (rng.standard_normal((nr, nc)) / np.sqrt(nc)).astype(np.float32)
+    x = np.abs(rng.standard_normal((nc, m))) * (rng.random((nc, m)) < 0.7)
+    Y = (B.astype(np.float64) @ x + 0.01 * rng.standard_normal((nr, m))).astype(np.float32)
+    return B, Y
+
+
+@pytest.mark.parametrize("nr,nc,m", [(512, 512, 1), (300, 257, 3), (1000, 64, 8), (33, 700, 2)])
+def test_dense_spgd_matches_oracle(nr, nc, m):
+    B, Y = _instance(nr, nc, m, seed=nr + nc + m)
+    X, G, loss, ms = dode.dense_nnls(B, Y, 60, 0.05)
+    Xo, Go, lo = spgd_dense(B, Y, 60, 0.05)
+    # loss: 1e-5 relative, with a floor at FP32 resolution of the problem's scale
+    # (1e-8 of ||y||^2) for underdetermined cases whose loss goes to ~0
+    floor = 1e-8 * (Y.astype(np.float64) ** 2).sum(axis=0)
+    np.testing.assert_allclose(loss, lo, rtol=1e-5, atol=floor.max())
+    assert rel_norm(X, Xo, axis=0).max() < 1e-4
+    assert np.all(X >= 0) and ms > 0
+    # continuing from the returned state equals a longer run
+    X2, G2, loss2, _ = dode.dense_nnls(B, Y, 40, 0.05, X0=X, G0=G)
+    Xo2, _, lo2 = spgd_dense(B, Y, 100, 0.05)
+    np.testing.assert_allclose(loss2, lo2, rtol=1e-5, atol=floor.max())
+    assert rel_norm(X2, Xo2, axis=0).max() < 1e-4
+
+
+def test_dense_spgd_device_pointers_and_errors():
+    torch = pytest.importorskip("torch")
+    B, Y = _instance(256, 256, 2, seed=5)
+    Xh, _, lh, _ = dode.dense_nnls(B, Y, 30, 0.05)
+    Bd, Yd = torch.from_numpy(B).cuda(), torch.from_numpy(Y).cuda()
+    Xd, Gd, ld, _ = dode.dense_nnls(Bd, Yd, 30, 0.05)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Xd.cpu().numpy(), Xh)
+    np.testing.assert_array_equal(ld.cpu().numpy(), lh)
+    with pytest.raises(dode.DodeError) as e:
+        dode.dense_nnls(B, np.zeros((256, 9), np.float32), 1, 0.05)      # more than 8 right-hand sides
+    assert e.value.code == dode.ERR_ARG

@@ -547,3 +547,35 @@ def test_pattern_dtheta_matches_finite_differences():
     d1 = (loss_at(0.1 + h) - loss_at(0.1 - h)) / (2 * h)
     d2 = (loss_at(0.1 + h / 2) - loss_at(0.1 - h / 2)) / h
     assert dth == pytest.approx((4 * d2 - d1) / 3, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# dense NNLS by Algorithm 1 (the paper's efficiency experiment)
+# ---------------------------------------------------------------------------
+
+def test_dense_spgd_pins():
+    from oracle.dense_nnls import spgd_dense
+    rng = np.random.default_rng(8)
+    # one step from 0 has a closed form: x = max(-eta g / (|g| + eps), 0), g = -B^T y
+    B = rng.standard_normal((7, 5))
+    y = rng.standard_normal((7, 1))
+    X, G, _ = spgd_dense(B, y, 1, step=0.3)
+    g = -B.T @ y
+    np.testing.assert_allclose(X, np.maximum(-0.3 * g / (np.abs(g) + 1e-10), 0.0), rtol=1e-15)
+    np.testing.assert_allclose(G, g * g, rtol=1e-15)
+    # exact recovery: y = B x_true, x_true >= 0, B well conditioned
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    Bw = Q * np.linspace(1.0, 2.0, 12)
+    x_true = np.abs(rng.standard_normal((12, 2)))
+    x_true[3, 0] = 0.0
+    X, _, loss = spgd_dense(Bw, Bw @ x_true, 4000, step=0.5)
+    np.testing.assert_allclose(X, x_true, atol=1e-7)
+    assert loss.max() < 1e-12
+    # noisy data: the NNLS minimiser (Lawson-Hanson) and its KKT conditions
+    sp_opt = pytest.importorskip("scipy.optimize")
+    yn = Bw @ x_true[:, :1] + 0.3 * rng.standard_normal((12, 1))
+    X, _, _ = spgd_dense(Bw, yn, 20000, step=0.5)
+    xs, _ = sp_opt.nnls(Bw, yn[:, 0])
+    np.testing.assert_allclose(X[:, 0], xs, atol=1e-6)
+    grad = Bw.T @ (Bw @ X[:, 0] - yn[:, 0])
+    assert np.all(grad > -1e-6) and np.all(np.abs(grad[X[:, 0] > 1e-8]) < 1e-6)
