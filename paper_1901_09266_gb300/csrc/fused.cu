@@ -6,15 +6,20 @@
 // of that day's epochs before taking the next one (days are independent
 // problems, Sec. 2.7).  One epoch is a forward sweep and an adjoint sweep:
 //
-//  * A task is (OD pair, tile of 31 departure intervals).  Its warp walks every
-//    route of the OD; lane l follows the leading vehicle that departs at
-//    boundary b0 + l (Example "DAR matrix computation").  At each link the lane's
-//    entry time T_j(b) and its right neighbour's T_j(b+1) (one shuffle) bound
-//    the window of Eq. (dar); the entry interval selects the link time from the
-//    tick table (Sec. 2.4, Eq. (cost)).  The route's links are held in registers
-//    as precomputed shared-memory offsets and broadcast by shuffles, so a link
-//    step touches memory only for the tick lookup and the window's one or two
-//    link-interval cells.  The OD / route tables sit in shared memory.
+//  * Routes leaving one origin share their trajectories over their common
+//    link prefix, so each origin's routes are walked as a prefix tree (walk
+//    groups, built once per network): every shared window is computed once.
+//  * A task is (walk group, the phase's tiles of 31 departure intervals):
+//    lane l follows the leading vehicles that depart at boundaries b0 + l and
+//    b0 + 31 + l (Example "DAR matrix computation") -- two independent chains
+//    per lane that share the route records, for instruction-level
+//    parallelism.  At each link a chain's entry time T_j(b) and its right
+//    neighbour's T_j(b+1) (one shuffle) bound the window of Eq. (dar); the
+//    entry interval selects the link time from the tick table (Sec. 2.4,
+//    Eq. (cost)).  The route's links are held in registers as precomputed
+//    shared-memory offsets and broadcast by shuffles, so a link step touches
+//    memory only for the tick lookup and the window's one or two link-interval
+//    cells.  The walk-group and route tables sit in shared memory.
 //  * Both sweeps run in phases of F tiles in time order.  A phase stages the
 //    tick rows its trajectories can reach (departure rows plus the day's
 //    largest trip offset, padded past the end of the day with the last row)
@@ -354,23 +359,16 @@ __device__ __forceinline__ int walk_start(const FusedParams &p, const int32_t *t
     return stk[s0];
 }
 
-// Forward task: walk group g for departure boundaries b0 .. b0 + 31.
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
-__device__ void forward_task(const FusedParams &p, const Shared &s, int day, int g, int b0, const int32_t *tab) {
-    const int lane = threadIdx.x & 31;
-    const int b = b0 + lane;
-    const int bb = min(b, p.N);
-    const bool vw = (lane < kTileW) && (b < p.N);
+// Route flows of one tile: exclusive prefix sums S over the group's walk order.
+template <int PREC>
+__device__ __forceinline__ void group_flows(const FusedParams &p, const Shared &s, int day, int i0, int m, int b,
+                                            bool vw, long long *S, bool &any, bool &fast) {
     const int bi = min(b, p.N - 1);
-    const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
-    const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
-    // route flows f = p q (Eq. (flow)) in 2^-20 vehicle units and their
-    // exclusive prefix sums over the group's walk order
-    long long S[kGroupRoutes + 1];
     long long acc = 0;
-    bool nonneg = true, any = false;
+    bool nonneg = true;
+    any = false;
     S[0] = 0;
-    for (int t0 = 0; t0 < m; t0 += 4) {                   // four routes' loads in flight
+    for (int t0 = 0; t0 < m; t0 += 4) {
         float pv[4], qv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -393,8 +391,25 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
             }
         }
     }
+    fast = nonneg && acc < (1ll << 31);
+}
+
+// Forward task: walk group g for departure boundaries b0 .. b0 + 31.
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ void forward_task(const FusedParams &p, const Shared &s, int day, int g, int b0, const int32_t *tab) {
+    const int lane = threadIdx.x & 31;
+    const int b = b0 + lane;
+    const int bb = min(b, p.N);
+    const bool vw = (lane < kTileW) && (b < p.N);
+    const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
+    const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    // route flows f = p q (Eq. (flow)) in 2^-20 vehicle units and their
+    // exclusive prefix sums over the group's walk order
+    long long S[kGroupRoutes + 1];
+    bool any, fast_lane;
+    group_flows<PREC>(p, s, day, i0, m, b, vw, S, any, fast_lane);
     if (!__any_sync(0xffffffffu, any)) return;            // nothing departs: no deposits
-    const bool fast = __all_sync(0xffffffffu, nonneg && acc < (1ll << 31));
+    const bool fast = __all_sync(0xffffffffu, fast_lane);
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
     int stk[kMaxRouteLinks + 1];
     for (int t = 0; t < m; ++t) {
@@ -414,6 +429,131 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
         else
             forward_walk_f<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trow, rr, gacc, s0, beta, T, vw, S, t,
                                                                    E, stk);
+    }
+}
+
+
+// Two tiles of the same walk group in one warp (A: boundaries b0 .., B: b0 + 31 ..):
+// the route record shuffles and loop control are shared, the two lane chains
+// are independent.  Integer form, routes of at most 32 links.
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                                const int32_t *trowA, const int32_t *trowB, const RouteRegs &rr,
+                                                float *gacc, int j0, int beta, int TA, int TB, bool vwA, bool vwB,
+                                                const long long *SA, const long long *SB, int t, int E, int *stkA,
+                                                int *stkB) {
+    const int lane = threadIdx.x & 31;
+    const int ipt = p.div.ipt, N = p.N;
+    uint32_t WuA = (uint32_t)(SA[E + 1] - SA[t]), WuB = (uint32_t)(SB[E + 1] - SB[t]);
+    float WfA = __uint2float_rn(WuA), WfB = __uint2float_rn(WuB);
+    for (int j = j0; j < beta; ++j) {
+        const int tb = __shfl_sync(0xffffffffu, rr.t0, j & 31);
+        const int ob = __shfl_sync(0xffffffffu, rr.o0, j & 31);
+        const int ev = __shfl_sync(0xffffffffu, rr.e0, j & 31);
+        if ((ev >> 1) != E) {
+            E = ev >> 1;
+            WuA = (uint32_t)(SA[E + 1] - SA[t]);
+            WuB = (uint32_t)(SB[E + 1] - SB[t]);
+            WfA = __uint2float_rn(WuA);
+            WfB = __uint2float_rn(WuB);
+        }
+        const int hiA = __shfl_down_sync(0xffffffffu, TA, 1);
+        const int hiB = __shfl_down_sync(0xffffffffu, TB, 1);
+        const int h0A = interval_of(TA, p.div);
+        const int h0B = interval_of(TB, p.div);
+        if (ob != kInactive) {
+            uint32_t u0A = 0, giveA = 0, u0B = 0, giveB = 0;
+            int kindA = 0, kindB = 0, e0A = 0, e0B = 0;
+            float invA = 0.f, invB = 0.f;
+            if (SMEM_RING || (vwA && h0A < N)) {
+                e0A = h0A * ipt + ipt;
+                invA = __fdividef(1.f, (float)(hiA - TA));
+                u0A = min(__float2uint_rn(WfA * first_share<PREC>(TA, e0A, invA)), WuA);
+                if (hiA > e0A && (SMEM_RING || h0A + 1 < N)) {
+                    if (hiA < e0A + ipt)
+                        giveA = WuA - u0A;
+                    else
+                        kindA = hiA == e0A + ipt ? 1 : 2;
+                }
+            }
+            if (SMEM_RING || (vwB && h0B < N)) {
+                e0B = h0B * ipt + ipt;
+                invB = __fdividef(1.f, (float)(hiB - TB));
+                u0B = min(__float2uint_rn(WfB * first_share<PREC>(TB, e0B, invB)), WuB);
+                if (hiB > e0B && (SMEM_RING || h0B + 1 < N)) {
+                    if (hiB < e0B + ipt)
+                        giveB = WuB - u0B;
+                    else
+                        kindB = hiB == e0B + ipt ? 1 : 2;
+                }
+            }
+            uint32_t recvA = __shfl_up_sync(0xffffffffu, giveA, 1);
+            uint32_t recvB = __shfl_up_sync(0xffffffffu, giveB, 1);
+            if (lane == 0) {
+                recvA = 0;
+                recvB = 0;
+            }
+            const uint32_t depA = u0A + recvA, depB = u0B + recvB;
+            if (depA) deposit_u<SMEM_RING>(s, gacc, ob + h0A, depA);
+            if (depB) deposit_u<SMEM_RING>(s, gacc, ob + h0B, depB);
+            if (kindA == 1)
+                deposit_u<SMEM_RING>(s, gacc, ob + h0A + 1, WuA - u0A);
+            else if (kindA == 2)
+                window_tail_u<PREC, SMEM_RING>(s, gacc, ob + h0A + 1, hiA, e0A, h0A + 1, N, ipt, invA, WfA, WuA - u0A);
+            if (kindB == 1)
+                deposit_u<SMEM_RING>(s, gacc, ob + h0B + 1, WuB - u0B);
+            else if (kindB == 2)
+                window_tail_u<PREC, SMEM_RING>(s, gacc, ob + h0B + 1, hiB, e0B, h0B + 1, N, ipt, invB, WfB, WuB - u0B);
+        }
+        TA = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowA, j, TA, tb, h0A);
+        TB = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowB, j, TB, tb, h0B);
+        if (ev & 1) {
+            stkA[j + 1] = TA;
+            stkB[j + 1] = TB;
+        }
+    }
+}
+
+// Forward task over both tiles of a phase for walk group g (b0 .. b0 + 61).
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ void forward_task2(const FusedParams &p, const Shared &s, int day, int g, int b0, const int32_t *tab) {
+    const int lane = threadIdx.x & 31;
+    const int bA = b0 + lane, bB = b0 + kTileW + lane;
+    const int bbA = min(bA, p.N), bbB = min(bB, p.N);
+    const bool vwA = (lane < kTileW) && (bA < p.N), vwB = (lane < kTileW) && (bB < p.N);
+    const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
+    const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    long long SA[kGroupRoutes + 1], SB[kGroupRoutes + 1];
+    bool anyA, anyB, fastA, fastB;
+    group_flows<PREC>(p, s, day, i0, m, bA, vwA, SA, anyA, fastA);
+    group_flows<PREC>(p, s, day, i0, m, bB, vwB, SB, anyB, fastB);
+    if (!__any_sync(0xffffffffu, anyA || anyB)) return;
+    if (!__all_sync(0xffffffffu, fastA && fastB)) {
+        forward_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0, tab);
+        forward_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0 + kTileW, tab);
+        return;
+    }
+    float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
+    int stkA[kMaxRouteLinks + 1], stkB[kMaxRouteLinks + 1];
+    for (int t = 0; t < m; ++t) {
+        const int4 gr = s.groute[i0 + t];
+        const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        if (s0 >= beta) continue;
+        const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
+        const int32_t *trowA = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bbA : nullptr;
+        const int32_t *trowB = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bbB : nullptr;
+        const int TA = walk_start<TAB>(p, trowA, stkA, s0, bbA);
+        const int TB = walk_start<TAB>(p, trowB, stkB, s0, bbB);
+        const int E = __shfl_sync(0xffffffffu, s0 < 32 ? rr.e0 : rr.e1, s0 & 31) >> 1;
+        if (beta <= 32) {
+            forward_walk_u2<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trowA, trowB, rr, gacc, s0, beta, TA, TB,
+                                                             vwA, vwB, SA, SB, t, E, stkA, stkB);
+        } else {
+            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowA, rr, gacc, s0, beta, TA, vwA,
+                                                                   SA, t, E, stkA);
+            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowB, rr, gacc, s0, beta, TB, vwB,
+                                                                   SB, t, E, stkB);
+        }
     }
 }
 
@@ -546,6 +686,124 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
                             [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
                             [&](int i) { return gpl[__ldg(&gr[i])]; }, dth);
         }
+    }
+    if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
+}
+
+
+// Adjoint walk of one route for two tiles of the same group (see forward_walk_u2).
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared &s, const int32_t *tick_day,
+                                              const int32_t *trowA, const int32_t *trowB, const RouteRegs &rr,
+                                              const void *rb, int j0, int beta, int TA, int TB, float &GA, float &GB,
+                                              bool vwA, bool vwB, int *stkA, int *stkB, float *gstkA, float *gstkB) {
+    const int ipt = p.div.ipt, N = p.N;
+    const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
+    for (int j = j0; j < beta; ++j) {
+        const int tb = __shfl_sync(0xffffffffu, rr.t0, j & 31);
+        const int ob = __shfl_sync(0xffffffffu, rr.o0, j & 31);
+        const int ev = __shfl_sync(0xffffffffu, rr.e0, j & 31);
+        const int hiA = __shfl_down_sync(0xffffffffu, TA, 1);
+        const int hiB = __shfl_down_sync(0xffffffffu, TB, 1);
+        const int h0A = interval_of(TA, p.div);
+        const int h0B = interval_of(TB, p.div);
+        if (ob != kInactive) {
+            if (SMEM_RING || (vwA && h0A < N)) {
+                const int idx = ob + h0A;
+                const int e0 = h0A * ipt + ipt;
+                const float inv = __fdividef(1.f, (float)(hiA - TA));
+                const float d0 = first_share<PREC>(TA, e0, inv);
+                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                if (hiA > e0 && (SMEM_RING || h0A + 1 < N)) {
+                    if (hiA <= e0 + ipt)
+                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                    else
+                        a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiA, e0, h0A + 1, N, ipt, inv,
+                                                                 d0, 0.f);
+                }
+                GA += a;
+            }
+            if (SMEM_RING || (vwB && h0B < N)) {
+                const int idx = ob + h0B;
+                const int e0 = h0B * ipt + ipt;
+                const float inv = __fdividef(1.f, (float)(hiB - TB));
+                const float d0 = first_share<PREC>(TB, e0, inv);
+                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                if (hiB > e0 && (SMEM_RING || h0B + 1 < N)) {
+                    if (hiB <= e0 + ipt)
+                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                    else
+                        a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiB, e0, h0B + 1, N, ipt, inv,
+                                                                 d0, 0.f);
+                }
+                GB += a;
+            }
+        }
+        TA = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowA, j, TA, tb, h0A);
+        TB = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowB, j, TB, tb, h0B);
+        if (ev & 1) {
+            stkA[j + 1] = TA;
+            gstkA[j + 1] = GA;
+            stkB[j + 1] = TB;
+            gstkB[j + 1] = GB;
+        }
+    }
+}
+
+// Adjoint task over both tiles of a phase for walk group g (b0 .. b0 + 61).
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
+__device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, int g, int b0, const void *rb,
+                              const int32_t *tab, double *s_dth) {
+    const int lane = threadIdx.x & 31;
+    const int bA = b0 + lane, bB = b0 + kTileW + lane;
+    const int bbA = min(bA, p.N), bbB = min(bB, p.N);
+    const bool vwA = (lane < kTileW) && (bA < p.N), vwB = (lane < kTileW) && (bB < p.N);
+    const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
+    const int N = p.N;
+    const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    float *gp = p.gp + (size_t)blockIdx.x * p.P * p.Np;
+    int stkA[kMaxRouteLinks + 1], stkB[kMaxRouteLinks + 1];
+    float gstkA[kMaxRouteLinks + 1], gstkB[kMaxRouteLinks + 1];
+    float gplA[kGroupRoutes], gplB[kGroupRoutes];
+    for (int t = 0; t < m; ++t) {
+        const int4 gr = s.groute[i0 + t];
+        const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
+        const int32_t *trowA = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bbA : nullptr;
+        const int32_t *trowB = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bbB : nullptr;
+        const int TA = walk_start<TAB>(p, trowA, stkA, s0, bbA);
+        const int TB = walk_start<TAB>(p, trowB, stkB, s0, bbB);
+        float GA = s0 == 0 ? 0.f : gstkA[s0];
+        float GB = s0 == 0 ? 0.f : gstkB[s0];
+        if (beta <= 32) {
+            adjoint_walk2<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trowA, trowB, rr, rb, s0, beta, TA, TB, GA,
+                                                           GB, vwA, vwB, stkA, stkB, gstkA, gstkB);
+        } else {
+            GA = adjoint_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowA, rr, rb, s0, beta, TA, GA,
+                                                                      vwA, stkA, gstkA);
+            GB = adjoint_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowB, rr, rb, s0, beta, TB, GB,
+                                                                      vwB, stkB, gstkB);
+        }
+        gplA[t] = GA;
+        gplB[t] = GB;
+        if (!((gr.w >> 8) & 1)) {
+            if (vwA) gp[(size_t)k * p.Np + bA] = GA;
+            if (vwB) gp[(size_t)k * p.Np + bB] = GB;
+        }
+    }
+    const int e0 = __ldg(&p.god_ptr[g]), e1 = __ldg(&p.god_ptr[g + 1]);
+    if (e0 == e1) return;
+    double dth = 0.0;
+    for (int e = e0; e < e1; ++e) {
+        const int r0 = __ldg(&p.godr_ptr[e]);
+        const int *gr = p.godr + r0;
+        const int od = __ldg(&p.god[e]), nr = __ldg(&p.godr_ptr[e + 1]) - r0;
+        if (vwA)
+            od_update<PREC>(p, day, od, bA, nr, [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
+                            [&](int i) { return gplA[__ldg(&gr[i])]; }, dth);
+        if (vwB)
+            od_update<PREC>(p, day, od, bB, nr, [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
+                            [&](int i) { return gplB[__ldg(&gr[i])]; }, dth);
     }
     if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
 }
@@ -1023,7 +1281,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             float ks = 0.f, kc = 0.f;  // solve: compensated FP32 sum
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
-                const int ntask = nt * p.n_groups;
+                const bool pairs = (nt & 1) == 0;
+                const int per_g = pairs ? nt / 2 : nt;
+                const int ntask = per_g * p.n_groups;
                 s.pb = pb0;
                 if (SMEM_TICKS && !tab) {
                     stage_ticks(p, s, tick16_day);
@@ -1034,12 +1294,20 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int g = task_grp[t / nt];
-                    const int b0 = pb0 + (t % nt) * kTileW;
-                    if (tab)
-                        forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, tab);
-                    else
-                        forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, tab);
+                    const int g = task_grp[t / per_g];
+                    if (pairs) {
+                        const int b0 = pb0 + (t % per_g) * 2 * kTileW;
+                        if (tab)
+                            forward_task2<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, tab);
+                        else
+                            forward_task2<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, tab);
+                    } else {
+                        const int b0 = pb0 + (t % nt) * kTileW;
+                        if (tab)
+                            forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, tab);
+                        else
+                            forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, tab);
+                    }
                 }
                 __syncthreads();
                 // rows [pb0, pb0 + 31 nt) are final: residual, loss, residual slot;
@@ -1106,7 +1374,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             // ------------------------------ adjoint sweep ------------------------------
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
-                const int ntask = nt * p.n_groups;
+                const bool pairs = (nt & 1) == 0;
+                const int per_g = pairs ? nt / 2 : nt;
+                const int ntask = per_g * p.n_groups;
                 s.pb = pb0;
                 __syncthreads();                           // previous phase done with the windows
                 if (SMEM_TICKS && !tab) stage_ticks(p, s, tick16_day);
@@ -1117,12 +1387,20 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int g = task_grp[t / nt];
-                    const int b0 = pb0 + (t % nt) * kTileW;
-                    if (tab)
-                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, rb, tab, &s_dth);
-                    else
-                        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, rb, tab, &s_dth);
+                    const int g = task_grp[t / per_g];
+                    if (pairs) {
+                        const int b0 = pb0 + (t % per_g) * 2 * kTileW;
+                        if (tab)
+                            adjoint_task2<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, rb, tab, &s_dth);
+                        else
+                            adjoint_task2<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, rb, tab, &s_dth);
+                    } else {
+                        const int b0 = pb0 + (t % nt) * kTileW;
+                        if (tab)
+                            adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, rb, tab, &s_dth);
+                        else
+                            adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, rb, tab, &s_dth);
+                    }
                 }
                 __syncthreads();
                 if (threadIdx.x == 0) s_task = 0;
