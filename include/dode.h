@@ -207,16 +207,21 @@ int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, flo
  *   X          [n_cols][m] FP32, in: the starting point, out: the iterate after `iters` steps
  *   G          [n_cols][m] FP32 Adagrad accumulator in/out, or NULL to start from 0
  *   loss       [m] FP64 out: ||B x_j - y_j||^2 of the final iterate
+ *   method     0 = automatic, 1 = one pass over B per iteration (rows of B are
+ *              streamed into shared memory by bulk asynchronous copies and used
+ *              for both products; needs m = 1, n_cols % 4 == 0, n_cols <= 8192 and
+ *              a 16-byte aligned B, else DODE_ERR_UNSUPPORTED), 2 = two passes
+ *              (one per product).  Automatic takes one pass when it applies.
  *   kernel_ms  out (may be NULL): GPU time of the iterations and the final residual
  * All arrays are host or device pointers per ptr_kind; stream is a cudaStream_t
  * (NULL = default stream); the call returns when its work is complete.
  * Limits: 1 <= m <= 8 and n_cols * m <= 51200 (x is staged in shared memory).
- * Errors: DODE_ERR_ARG, DODE_ERR_UNSUPPORTED (the limit), DODE_ERR_OOM, DODE_ERR_CUDA;
- * the message goes to stderr.
+ * Errors: DODE_ERR_ARG, DODE_ERR_UNSUPPORTED (the limits), DODE_ERR_OOM, DODE_ERR_CUDA,
+ * DODE_ERR_DEVICE_TIMEOUT (a bounded wait for a bulk copy expired); the message goes to stderr.
  */
 int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, const float *Y, int32_t iters,
-                    float step, float eps, float *X, float *G, double *loss, double *kernel_ms, int32_t ptr_kind,
-                    void *stream);
+                    float step, float eps, int32_t method, float *X, float *G, double *loss, double *kernel_ms,
+                    int32_t ptr_kind, void *stream);
 
 /*
  * dode_set_patterns -- traffic patterns of the loaded days (Step 2-3 of the

@@ -1310,15 +1310,16 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
 }
 
 int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, const float *Y, int32_t iters,
-                    float step, float eps, float *X, float *G, double *loss, double *kernel_ms, int32_t ptr_kind,
-                    void *stream) {
+                    float step, float eps, int32_t method, float *X, float *G, double *loss, double *kernel_ms,
+                    int32_t ptr_kind, void *stream) {
     auto bail = [&](int code, const std::string &msg) {
         fprintf(stderr, "dode_dense_nnls: %s\n", msg.c_str());
         return code;
     };
     if (n_rows < 1 || n_cols < 1 || m < 1 || m > 8 || iters < 0 || !(step > 0.f) || !std::isfinite(step) ||
-        !(eps >= 0.f) || !B || !Y || !X || !loss || (ptr_kind != DODE_PTR_HOST && ptr_kind != DODE_PTR_DEVICE))
-        return bail(DODE_ERR_ARG, "arguments (1 <= m <= 8, iters >= 0, step > 0)");
+        !(eps >= 0.f) || !B || !Y || !X || !loss || (ptr_kind != DODE_PTR_HOST && ptr_kind != DODE_PTR_DEVICE) ||
+        method < 0 || method > 2)
+        return bail(DODE_ERR_ARG, "arguments (1 <= m <= 8, iters >= 0, step > 0, method 0..2)");
     if ((long long)n_cols * m * sizeof(float) > 200 * 1024)
         return bail(DODE_ERR_UNSUPPORTED, "n_cols * m must be at most 51200 (x is staged in shared memory)");
     int dev = 0, n_sm = 0;
@@ -1336,30 +1337,51 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     // row blocks of 32 rows (8 rows per load batch); partial gradients per block
     p.rows_per_cta = 32;
     p.grid_g = (n_rows + p.rows_per_cta - 1) / p.rows_per_cta;
-    // one device allocation: (B, y when on the host) x, G, r, partials, loss
+    // one pass over B per iteration (bulk-copy staged) when it applies
     const bool host = ptr_kind == DODE_PTR_HOST;
-    const size_t f_count = (host ? nB + nY : 0) + nX + nX + nY + (size_t)p.grid_g * nX;
-    const size_t d_count = (size_t)p.grid_r * m + m;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t xbytes = ((size_t)n_cols * 4 + 127) & ~(size_t)127;
+    const size_t room = (size_t)optin > xbytes + 1024 ? (size_t)optin - xbytes - 1024 : 0;
+    const int RB = (int)std::min<size_t>(8, room / ((size_t)2 * n_cols * 4));
+    const bool one_ok = m == 1 && n_cols % 4 == 0 && n_cols <= 8192 && RB >= 1 &&
+                        (host || ((uintptr_t)B % 16 == 0));
+    if (method == 1 && !one_ok)
+        return bail(DODE_ERR_UNSUPPORTED, "one pass needs m = 1, n_cols % 4 == 0, n_cols <= 8192, 16-byte aligned B");
+    const bool one = method == 1 || (method == 0 && one_ok);
+    const int grid_f = n_sm;
+    // one device allocation: (B, y when on the host) x, G, r, gradient partials, loss
+    // partials (of either kernel), loss, error flag; every piece starts on a
+    // 256-byte boundary (the kernels use 16-byte accesses)
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        const size_t o = off;
+        off += (n + 63) & ~(size_t)63;
+        return o;
+    };
+    const size_t oB = host ? take(nB) : 0, oY = host ? take(nY) : 0;
+    const size_t oX = take(nX), oG = take(nX), oR = take(nY);
+    const size_t oP = take((size_t)std::max(p.grid_g, grid_f) * nX);
+    const size_t n_lpart = (size_t)std::max(p.grid_r, grid_f) * m;
+    const size_t d_count = n_lpart + m + 1;
     char *buf = nullptr;
-    const size_t f_bytes = (f_count * sizeof(float) + 255) & ~(size_t)255;
+    const size_t f_bytes = off * sizeof(float);
     if (cudaMalloc(&buf, f_bytes + d_count * sizeof(double)) != cudaSuccess) {
         (void)cudaGetLastError();
         return bail(DODE_ERR_OOM, "device memory");
     }
     float *f = reinterpret_cast<float *>(buf);
-    p.B = host ? f : B;
-    if (host) f += nB;
-    p.y = host ? f : Y;
-    if (host) f += nY;
-    p.x = f;
-    f += nX;
-    p.G = f;
-    f += nX;
-    p.r = f;
-    f += nY;
-    p.gpart = f;
+    p.B = host ? f + oB : B;
+    p.y = host ? f + oY : Y;
+    p.x = f + oX;
+    p.G = f + oG;
+    p.r = f + oR;
+    p.gpart = f + oP;
+    p.vec = n_cols % 4 == 0 && ((uintptr_t)p.B % 16 == 0) ? 1 : 0;
     p.lpart = reinterpret_cast<double *>(buf + f_bytes);
-    double *dloss = p.lpart + (size_t)p.grid_r * m;
+    double *dloss = p.lpart + n_lpart;
+    int *derr = reinterpret_cast<int *>(dloss + m);
+    const size_t fsmem = xbytes + (size_t)2 * RB * n_cols * 4;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaSuccess;
@@ -1369,10 +1391,13 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     if (e == cudaSuccess)
         e = G ? cudaMemcpyAsync(p.G, G, nX * sizeof(float), in, st) : cudaMemsetAsync(p.G, 0, nX * sizeof(float), st);
     if (e == cudaSuccess) e = dense_set_smem((size_t)n_cols * m * sizeof(float), (size_t)p.rows_per_cta * m * sizeof(float));
+    if (e == cudaSuccess && one) e = dense_fused_set_smem(fsmem);
+    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    for (int it = 0; it < iters && e == cudaSuccess; ++it) e = dense_iteration(p, true, st);
+    for (int it = 0; it < iters && e == cudaSuccess; ++it)
+        e = one ? dense_fused_iteration(p, grid_f, RB, fsmem, derr, st) : dense_iteration(p, true, st);
     if (e == cudaSuccess) e = dense_iteration(p, false, st);     // residual and loss of the final x
     if (e == cudaSuccess) e = dense_loss(p, dloss, st);
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -1381,6 +1406,8 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     if (e == cudaSuccess && G) e = cudaMemcpyAsync(G, p.G, nX * sizeof(float), out, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dloss, m * sizeof(double), host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
     float ms = 0.f;
     if (e == cudaSuccess && kernel_ms) {
         e = cudaEventElapsedTime(&ms, e0, e1);
@@ -1393,6 +1420,7 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
         (void)cudaGetLastError();
         return bail(DODE_ERR_CUDA, cudaGetErrorString(e));
     }
+    if (herr) return bail(DODE_ERR_DEVICE_TIMEOUT, "a bulk copy of B did not complete in time");
     return DODE_OK;
 }
 

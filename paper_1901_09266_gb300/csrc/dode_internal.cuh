@@ -171,11 +171,12 @@ struct DenseParams {
     float *x, *G, *r, *gpart;
     double *lpart;
     int nr, nc, m, grid_r, grid_g, rows_per_cta;
+    int vec;                   // rows of B start on 16-byte boundaries (n_cols % 4 == 0, aligned base)
     float eta, eps;
 };
 
 // error codes mirrored from dode.h for device use
-constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrUnsupported = -10;
+constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrDeviceTimeout = -8, kErrUnsupported = -10;
 
 __device__ __forceinline__ void set_error(int *err, int code, long long index) {
     if (atomicCAS(err, 0, code) == 0) {
@@ -210,6 +211,8 @@ cudaError_t launch_dar_distance(const DarParams &p, double *part, int n_part, do
 cudaError_t dense_iteration(const DenseParams &p, bool step, cudaStream_t s);
 cudaError_t dense_loss(const DenseParams &p, double *loss, cudaStream_t s);
 cudaError_t dense_set_smem(size_t resid_bytes, size_t grad_bytes);
+cudaError_t dense_fused_iteration(const DenseParams &p, int grid, int RB, size_t smem, int *err, cudaStream_t s);
+cudaError_t dense_fused_set_smem(size_t bytes);
 cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);

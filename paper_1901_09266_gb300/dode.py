@@ -86,7 +86,7 @@ def load(path: str = LIB_PATH):
         "dode_forward": (ct.c_int, [vp, vp, vp, i32]),
         "dode_loss": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_loss_grad": (ct.c_int, [vp, vp, f32, vp, vp, vp, i32]),
-        "dode_dense_nnls": (ct.c_int, [i32, i32, i32, vp, vp, i32, f32, f32, vp, vp, vp, vp, i32, vp]),
+        "dode_dense_nnls": (ct.c_int, [i32, i32, i32, vp, vp, i32, f32, f32, i32, vp, vp, vp, vp, i32, vp]),
         "dode_set_patterns": (ct.c_int, [vp, vp]),
         "dode_r2": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_dar_distance": (ct.c_int, [vp, vp, vp]),
@@ -352,8 +352,10 @@ class Context:
         self._check(load().dode_set_max_ctas(self.h, max_ctas))
 
 
-def dense_nnls(B, Y, iters: int, step: float, X0=None, G0=None, eps: float = 1e-10, stream=None):
-    """Algorithm 1 on a dense B for the columns of Y (dode_dense_nnls).
+def dense_nnls(B, Y, iters: int, step: float, X0=None, G0=None, eps: float = 1e-10, stream=None,
+               method: int = 0):
+    """Algorithm 1 on a dense B for the columns of Y (dode_dense_nnls); method
+    0 = automatic, 1 = one pass over B per iteration, 2 = two passes.
 
     numpy arrays run from host memory; CUDA torch tensors in place on the
     device.  Returns (X, G, loss, kernel_ms)."""
@@ -383,7 +385,7 @@ def dense_nnls(B, Y, iters: int, step: float, X0=None, G0=None, eps: float = 1e-
         raise ValueError("B and Y must have the same number of rows")
     ms = ct.c_double(0.0)
     rc = load().dode_dense_nnls(int(nr), int(nc), int(m), args[0], args[1], int(iters), float(step), float(eps),
-                                args[2], args[3], args[4], ct.addressof(ms), kind, st)
+                                int(method), args[2], args[3], args[4], ct.addressof(ms), kind, st)
     if rc != OK:
         raise DodeError(rc, "dode_dense_nnls failed (details on stderr)")
     return X, G, loss, ms.value

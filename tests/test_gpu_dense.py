@@ -55,3 +55,23 @@ def test_dense_spgd_device_pointers_and_errors():
     with pytest.raises(dode.DodeError) as e:
         dode.dense_nnls(B, np.zeros((256, 9), np.float32), 1, 0.05)      # more than 8 right-hand sides
     assert e.value.code == dode.ERR_ARG
+
+
+@pytest.mark.parametrize("nr,nc", [(512, 512), (1003, 1024), (130, 8192), (2000, 4)])
+def test_dense_one_pass_matches_two_passes_and_oracle(nr, nc):
+    """One pass over B per iteration (rows staged by bulk asynchronous copies)
+    against the two-pass kernels and the FP64 oracle; ragged row blocks and
+    the largest supported column count included."""
+    B, Y = _instance(nr, nc, 1, seed=nr * 7 + nc)
+    X1, G1, l1, _ = dode.dense_nnls(B, Y, 40, 0.05, method=1)
+    X2, G2, l2, _ = dode.dense_nnls(B, Y, 40, 0.05, method=2)
+    Xo, _, lo = spgd_dense(B, Y, 40, 0.05)
+    floor = 1e-8 * float((Y.astype(np.float64) ** 2).sum())
+    np.testing.assert_allclose(l1, lo, rtol=1e-5, atol=floor)
+    np.testing.assert_allclose(l2, lo, rtol=1e-5, atol=floor)
+    assert rel_norm(X1, Xo, axis=0).max() < 1e-4
+    assert rel_norm(X1, X2, axis=0).max() < 1e-5
+    # one pass does not apply to several right-hand sides
+    with pytest.raises(dode.DodeError) as e:
+        dode.dense_nnls(B, np.concatenate([Y, Y], axis=1), 1, 0.05, method=1)
+    assert e.value.code == dode.ERR_UNSUPPORTED
