@@ -453,6 +453,30 @@ def run_gpu(args):
                              "final_loss": float(ld.sum().item())}
         del Bd, Yd
 
+    # form 3 (differentiable) on the 600-OD / 1500-route / 1000-detector corridor:
+    # loss and gradients (dL/dq, dL/dtheta) of every day, DAR recomputed in both passes
+    form3 = None
+    if args.form3_days > 0 and rank == 0:
+        w5 = make_workload("corridor-large", args.form3_days)
+        d5 = list(range(args.form3_days))
+        sp5, ct5, mk5 = gpu_inputs(w5, d5)
+        c5 = dode.Context.from_workload(w5, precision=prec)
+        c5.use_torch_stream()
+        c5.set_days(ct5, sp5, mk5)
+        q5 = torch.from_numpy(w5.q_true(d5) * np.float32(0.9)).to(dev)
+        dq5 = torch.empty_like(q5)
+        c5.loss_grad(q5, 0.1, dq_out=dq5)                     # warm-up
+        ms5 = []
+        for _ in range(3):
+            loss5, _, dth5 = c5.loss_grad(q5, 0.1, dq_out=dq5)
+            ms5.append(c5.last_kernel_ms())
+        form3 = {"workload": w5.name, "days": len(d5), "routes": w5.routes.n_routes, "od_pairs": w5.routes.n_od,
+                 "detectors": w5.net.n_obs, "kernel_ms": min(ms5),
+                 "day_loss_grads_per_s": len(d5) / (min(ms5) / 1e3),
+                 "total_loss": float(np.sum(loss5)), "dtheta_total": float(np.sum(dth5))}
+        c5.close()
+        del q5, dq5
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
@@ -482,6 +506,7 @@ def run_gpu(args):
             "clocks": clk,
             "forms": forms,
             "next": nxt,
+            "form3": form3,
             "final_loss_total": final_loss,
         }
         print(json.dumps(line), flush=True)
@@ -513,6 +538,8 @@ def main(argv=None):
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with the autotuner")
     ap.add_argument("--compare-epochs", type=int, default=20)
     ap.add_argument("--next-rows", type=int, default=1, help="time the pattern, R^2, DAR-distance and dense rows")
+    ap.add_argument("--form3-days", type=int, default=152,
+                    help="days of the corridor-large loss+gradient timing (0 = skip)")
     ap.add_argument("--dense-n", type=int, default=6000)
     ap.add_argument("--dense-iters", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=2)

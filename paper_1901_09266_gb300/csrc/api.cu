@@ -524,6 +524,7 @@ FusedParams base_params(dode_ctx *ctx) {
     p.rev = ctx->d_rev;
     p.rod = ctx->d_rod;
     p.n_groups = ctx->G;
+    p.n_pair_groups = ctx->G;
     p.god_ptr = ctx->d_god_ptr;
     p.god = ctx->d_god;
     p.godr_ptr = ctx->d_godr_ptr;

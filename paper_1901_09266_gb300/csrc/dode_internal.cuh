@@ -75,6 +75,7 @@ struct FusedParams {
     const int32_t *rev;        // [L] (E << 1) | save of every route position (see build_groups)
     const int32_t *rod;        // [P] OD pair of each route
     int n_groups;
+    int n_pair_groups;         // the first ones of task_grp are walked as tile pairs
     const int32_t *god_ptr;    // [G+1] ODs owned by each group (all their routes are in it)
     const int32_t *god;        // owned ODs
     const int32_t *godr_ptr;   // routes of each owned OD in godr

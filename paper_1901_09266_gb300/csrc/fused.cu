@@ -1173,6 +1173,27 @@ __device__ int row_labels(const FusedParams &p, const uint32_t *mk, int gday, in
     return (int)((*s_n + b - 1) / b);
 }
 
+// Task t of a phase of nt tiles: the first nb groups of the processing order
+// (the largest walks) go as pairs of tiles when nt is even, the other groups
+// as single tiles, so the tail of a phase is made of small tasks.
+struct TaskRef {
+    int g, b0;
+    bool pair;
+};
+
+__device__ __forceinline__ int phase_tasks(int nt, int nb, int G) {
+    if (nt & 1) nb = 0;
+    return nb * (nt / 2) + (G - nb) * nt;
+}
+
+__device__ __forceinline__ TaskRef task_ref(int t, int nt, int nb, int pb0, const int *task_grp) {
+    if (nt & 1) nb = 0;
+    const int hp = nt / 2, np = nb * hp;
+    if (t < np) return TaskRef{task_grp[t / hp], pb0 + (t % hp) * 2 * kTileW, true};
+    t -= np;
+    return TaskRef{task_grp[nb + t / nt], pb0 + (t % nt) * kTileW, false};
+}
+
 // Dynamic shared memory layout (16-byte aligned blocks):
 //   groute int4[P] | gptr int[G+1] | task_grp int[G] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
@@ -1237,6 +1258,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         s_carry = 0;
     }
     const bool exact = p.mode != MODE_SOLVE;
+    const int nbg = p.n_pair_groups;                  // groups walked as tile pairs
 
     while (true) {
         __syncthreads();
@@ -1281,9 +1303,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             float ks = 0.f, kc = 0.f;  // solve: compensated FP32 sum
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
-                const bool pairs = (nt & 1) == 0;
-                const int per_g = pairs ? nt / 2 : nt;
-                const int ntask = per_g * p.n_groups;
+                const int ntask = phase_tasks(nt, nbg, p.n_groups);
                 s.pb = pb0;
                 if (SMEM_TICKS && !tab) {
                     stage_ticks(p, s, tick16_day);
@@ -1294,19 +1314,17 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int g = task_grp[t / per_g];
-                    if (pairs) {
-                        const int b0 = pb0 + (t % per_g) * 2 * kTileW;
+                    const TaskRef tr = task_ref(t, nt, nbg, pb0, task_grp);
+                    if (tr.pair) {
                         if (tab)
-                            forward_task2<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, tab);
+                            forward_task2<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, tr.g, tr.b0, tab);
                         else
-                            forward_task2<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, tab);
+                            forward_task2<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, tr.g, tr.b0, tab);
                     } else {
-                        const int b0 = pb0 + (t % nt) * kTileW;
                         if (tab)
-                            forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, tab);
+                            forward_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, tr.g, tr.b0, tab);
                         else
-                            forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, tab);
+                            forward_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, tr.g, tr.b0, tab);
                     }
                 }
                 __syncthreads();
@@ -1374,9 +1392,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             // ------------------------------ adjoint sweep ------------------------------
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
-                const bool pairs = (nt & 1) == 0;
-                const int per_g = pairs ? nt / 2 : nt;
-                const int ntask = per_g * p.n_groups;
+                const int ntask = phase_tasks(nt, nbg, p.n_groups);
                 s.pb = pb0;
                 __syncthreads();                           // previous phase done with the windows
                 if (SMEM_TICKS && !tab) stage_ticks(p, s, tick16_day);
@@ -1387,19 +1403,17 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
                     if (t >= ntask) break;
-                    const int g = task_grp[t / per_g];
-                    if (pairs) {
-                        const int b0 = pb0 + (t % per_g) * 2 * kTileW;
+                    const TaskRef tr = task_ref(t, nt, nbg, pb0, task_grp);
+                    if (tr.pair) {
                         if (tab)
-                            adjoint_task2<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, rb, tab, &s_dth);
+                            adjoint_task2<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, tr.g, tr.b0, rb, tab, &s_dth);
                         else
-                            adjoint_task2<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, rb, tab, &s_dth);
+                            adjoint_task2<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, tr.g, tr.b0, rb, tab, &s_dth);
                     } else {
-                        const int b0 = pb0 + (t % nt) * kTileW;
                         if (tab)
-                            adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, g, b0, rb, tab, &s_dth);
+                            adjoint_task<PREC, SMEM_RING, SMEM_TICKS, true>(p, s, day, tr.g, tr.b0, rb, tab, &s_dth);
                         else
-                            adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, g, b0, rb, tab, &s_dth);
+                            adjoint_task<PREC, SMEM_RING, SMEM_TICKS, false>(p, s, day, tr.g, tr.b0, rb, tab, &s_dth);
                     }
                 }
                 __syncthreads();
