@@ -144,8 +144,7 @@ __device__ __forceinline__ RouteRegs load_route(const FusedParams &p, const Shar
 template <int PREC>
 __device__ __forceinline__ float first_share(int T, int e0, float inv) {
     const float d = fminf(1.f, (float)(e0 - T) * inv);
-    if (PREC == 0) return d;
-    return d < 1.f ? bf16_round(d) : 1.f;
+    return PREC == 0 ? d : bf16_round(d);      // 1 is exact in BF16
 }
 
 // Add v to accumulator cell idx: 64-bit fixed point (shared low word, carries
@@ -260,10 +259,10 @@ __device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s,
 // ring rows that are never flushed and are cleared after the sweep.  LONG:
 // the route has more than 32 links (positions 32.. sit in the second register
 // set).
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG, class ST>
 __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
-                                               int T, bool vw, const long long *S, int t, int E, int *stk) {
+                                               int T, bool vw, const ST *S, int t, int E, int *stk) {
     const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.N;
     uint32_t Wu = (uint32_t)(S[E + 1] - S[t]);
@@ -359,10 +358,12 @@ __device__ __forceinline__ int walk_start(const FusedParams &p, const int32_t *t
     return stk[s0];
 }
 
-// Route flows of one tile: exclusive prefix sums S over the group's walk order.
-template <int PREC>
+// Route flows of one tile: exclusive prefix sums S over the group's walk order
+// (ST = uint32_t keeps the low words only: enough when the caller walks the
+// integer form, which needs fast).
+template <int PREC, class ST>
 __device__ __forceinline__ void group_flows(const FusedParams &p, const Shared &s, int day, int i0, int m, int b,
-                                            bool vw, long long *S, bool &any, bool &fast) {
+                                            bool vw, ST *S, bool &any, bool &fast) {
     const int bi = min(b, p.N - 1);
     long long acc = 0;
     bool nonneg = true;
@@ -387,7 +388,7 @@ __device__ __forceinline__ void group_flows(const FusedParams &p, const Shared &
                 nonneg = nonneg && fu >= 0;
                 any = any || fu != 0;
                 acc += fu;
-                S[t0 + u + 1] = acc;
+                S[t0 + u + 1] = (ST)acc;
             }
         }
     }
@@ -407,7 +408,7 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
     // exclusive prefix sums over the group's walk order
     long long S[kGroupRoutes + 1];
     bool any, fast_lane;
-    group_flows<PREC>(p, s, day, i0, m, b, vw, S, any, fast_lane);
+    group_flows<PREC, long long>(p, s, day, i0, m, b, vw, S, any, fast_lane);
     if (!__any_sync(0xffffffffu, any)) return;            // nothing departs: no deposits
     const bool fast = __all_sync(0xffffffffu, fast_lane);
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
@@ -440,11 +441,11 @@ template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                 const int32_t *trowA, const int32_t *trowB, const RouteRegs &rr,
                                                 float *gacc, int j0, int beta, int TA, int TB, bool vwA, bool vwB,
-                                                const long long *SA, const long long *SB, int t, int E, int *stkA,
+                                                const uint32_t *SA, const uint32_t *SB, int t, int E, int *stkA,
                                                 int *stkB) {
     const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.N;
-    uint32_t WuA = (uint32_t)(SA[E + 1] - SA[t]), WuB = (uint32_t)(SB[E + 1] - SB[t]);
+    uint32_t WuA = SA[E + 1] - SA[t], WuB = SB[E + 1] - SB[t];
     float WfA = __uint2float_rn(WuA), WfB = __uint2float_rn(WuB);
     for (int j = j0; j < beta; ++j) {
         const int tb = __shfl_sync(0xffffffffu, rr.t0, j & 31);
@@ -452,8 +453,8 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
         const int ev = __shfl_sync(0xffffffffu, rr.e0, j & 31);
         if ((ev >> 1) != E) {
             E = ev >> 1;
-            WuA = (uint32_t)(SA[E + 1] - SA[t]);
-            WuB = (uint32_t)(SB[E + 1] - SB[t]);
+            WuA = SA[E + 1] - SA[t];
+            WuB = SB[E + 1] - SB[t];
             WfA = __uint2float_rn(WuA);
             WfB = __uint2float_rn(WuB);
         }
@@ -523,10 +524,10 @@ __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, in
     const bool vwA = (lane < kTileW) && (bA < p.N), vwB = (lane < kTileW) && (bB < p.N);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
-    long long SA[kGroupRoutes + 1], SB[kGroupRoutes + 1];
+    uint32_t SA[kGroupRoutes + 1], SB[kGroupRoutes + 1];   // the pair walk is integer-form only
     bool anyA, anyB, fastA, fastB;
-    group_flows<PREC>(p, s, day, i0, m, bA, vwA, SA, anyA, fastA);
-    group_flows<PREC>(p, s, day, i0, m, bB, vwB, SB, anyB, fastB);
+    group_flows<PREC, uint32_t>(p, s, day, i0, m, bA, vwA, SA, anyA, fastA);
+    group_flows<PREC, uint32_t>(p, s, day, i0, m, bB, vwB, SB, anyB, fastB);
     if (!__any_sync(0xffffffffu, anyA || anyB)) return;
     if (!__all_sync(0xffffffffu, fastA && fastB)) {
         forward_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0, tab);
