@@ -66,7 +66,10 @@ typedef struct {
 /* One day's model: everything the speeds determine. */
 typedef struct {
     const or_net *net;
-    int32_t *ticks;       /* [N][A] link travel time in ticks, by entry interval */
+    int32_t Nh;           /* time horizon in intervals: N, or 2N when the next day is
+                             coupled (trips past midnight run on its speeds and land
+                             in its first intervals, rows N .. 2N-1 here) */
+    int32_t *ticks;       /* [Nh][A] link travel time in ticks, by entry interval */
     int64_t *T;           /* [(rptr[k]+k+j)][N+1] trajectory times, j = 0..beta_k */
     int64_t n_repairs;    /* FIFO repairs applied */
     or_dar_entry *dar;    /* DAR entries */
@@ -78,7 +81,7 @@ typedef struct {
     double *p;            /* [N][P] route choice portion */
     /* assignment matrix B (Eq. (assign)) in COO, observed rows only */
     int64_t nnz;
-    int32_t *b_row;       /* h2 * O + o */
+    int32_t *b_row;       /* h2 * O + o, h2 < Nh */
     int32_t *b_col;       /* h1 * K + od */
     double *b_val;
 } or_day;
@@ -138,10 +141,11 @@ int or_ticks(const or_net *n, const float *speed_mph /* [N][A] */, int32_t *tick
     return OR_OK;
 }
 
-/* c_a(t): travel time of link a for a vehicle entering it at tick t.       */
-static int64_t link_time(const or_net *n, const int32_t *ticks, int32_t a, int64_t t) {
+/* c_a(t): travel time of link a for a vehicle entering it at tick t; the    */
+/* table covers Nh intervals and its last row holds for later entries.      */
+static int64_t link_time(const or_net *n, const int32_t *ticks, int32_t Nh, int32_t a, int64_t t) {
     int64_t h = t / n->ipt;
-    if (h > n->N - 1) h = n->N - 1;
+    if (h > Nh - 1) h = Nh - 1;
     return ticks[h * n->A + a];
 }
 
@@ -155,7 +159,7 @@ static size_t traj_index(const or_net *n, int32_t k, int32_t j, int32_t b) {
 /* T_{k,j+1}(b) = T_{k,j}(b) + c_{a_{k,j}}(T_{k,j}(b)).  FIFO (Sec. 2.2) is   */
 /* enforced per link, in increasing b, by T_{k,j}(b) >= T_{k,j}(b-1).        */
 /* ------------------------------------------------------------------------ */
-void or_trajectories(const or_net *n, const int32_t *ticks, int64_t *T, int64_t *n_repairs) {
+void or_trajectories(const or_net *n, const int32_t *ticks, int32_t Nh, int64_t *T, int64_t *n_repairs) {
     int64_t rep = 0;
     for (int32_t k = 0; k < n->P; ++k) {
         int32_t beta = n->rptr[k + 1] - n->rptr[k];
@@ -164,7 +168,7 @@ void or_trajectories(const or_net *n, const int32_t *ticks, int64_t *T, int64_t 
             for (int32_t j = 0; j < beta; ++j) {
                 int32_t a = n->rlinks[n->rptr[k] + j];
                 int64_t t = T[traj_index(n, k, j, b)];
-                int64_t nxt = t + link_time(n, ticks, a, t);
+                int64_t nxt = t + link_time(n, ticks, Nh, a, t);
                 if (b > 0) {
                     int64_t prev = T[traj_index(n, k, j + 1, b - 1)];
                     if (nxt < prev) { nxt = prev; ++rep; }
@@ -181,9 +185,10 @@ void or_trajectories(const or_net *n, const int32_t *ticks, int64_t *T, int64_t 
 /* the tail of its j-th link spread evenly (Eq. (unif)) over the window     */
 /* [T_{k,j}(h1), T_{k,j}(h1+1)); rho(h1,h2) is the share of that window in   */
 /* H_{h2}.  A zero-length window puts all mass in the interval containing   */
-/* it.  Shares at h2 >= N (after midnight) are dropped.                     */
+/* it.  Shares at h2 >= Nh are dropped: after midnight (Nh = N), or past    */
+/* the end of the coupled next day (Nh = 2N).                               */
 /* ------------------------------------------------------------------------ */
-static int64_t dar_emit(const or_net *n, const int64_t *T, or_dar_entry *out) {
+static int64_t dar_emit(const or_net *n, int32_t Nh, const int64_t *T, or_dar_entry *out) {
     int64_t m = 0;
     const int64_t ipt = n->ipt;
     for (int32_t k = 0; k < n->P; ++k) {
@@ -194,13 +199,13 @@ static int64_t dar_emit(const or_net *n, const int64_t *T, or_dar_entry *out) {
                 int64_t hi = T[traj_index(n, k, j, h1 + 1)];
                 if (hi == lo) {
                     int64_t h2 = lo / ipt;
-                    if (h2 < n->N) {
+                    if (h2 < Nh) {
                         if (out) { out[m].k = k; out[m].j = j; out[m].h1 = h1; out[m].h2 = (int32_t)h2; out[m].rho = 1.0; }
                         ++m;
                     }
                     continue;
                 }
-                for (int64_t h2 = lo / ipt; h2 <= (hi - 1) / ipt && h2 < n->N; ++h2) {
+                for (int64_t h2 = lo / ipt; h2 <= (hi - 1) / ipt && h2 < Nh; ++h2) {
                     int64_t s = lo > ipt * h2 ? lo : ipt * h2;
                     int64_t e = hi < ipt * (h2 + 1) ? hi : ipt * (h2 + 1);
                     if (out) {
@@ -276,12 +281,18 @@ void or_day_set_choice_times(or_day *d, const double *Cc) {
     or_day_set_theta(d, d->theta);
 }
 
-/* Build one day's model from its speeds [N][A].  Returns NULL on error.     */
-or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int *err) {
+/* Build one day's model from its speeds [N][A]; with speed_next (the next  */
+/* day's speeds, or NULL) the day is coupled to the next one: the horizon   */
+/* covers both days (see or_solve_coupled).  Returns NULL on error.          */
+or_day *or_day_build_coupled(const or_net *n, const float *speed_mph, const float *speed_next, double theta,
+                             int *err) {
     or_day *d = (or_day *)calloc(1, sizeof(or_day));
     d->net = n;
-    d->ticks = (int32_t *)malloc(sizeof(int32_t) * (size_t)n->N * n->A);
+    d->Nh = speed_next ? 2 * n->N : n->N;
+    const size_t NA = (size_t)n->N * n->A;
+    d->ticks = (int32_t *)malloc(sizeof(int32_t) * (size_t)d->Nh * n->A);
     int rc = or_ticks(n, speed_mph, d->ticks);
+    if (rc == OR_OK && speed_next) rc = or_ticks(n, speed_next, d->ticks + NA);
     if (rc != OR_OK) {
         if (err) *err = rc;
         free(d->ticks); free(d);
@@ -289,10 +300,10 @@ or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int 
     }
     size_t ntraj = (size_t)(n->rptr[n->P] + n->P) * (size_t)(n->N + 1);
     d->T = (int64_t *)malloc(sizeof(int64_t) * ntraj);
-    or_trajectories(n, d->ticks, d->T, &d->n_repairs);
-    d->n_dar = dar_emit(n, d->T, NULL);
+    or_trajectories(n, d->ticks, d->Nh, d->T, &d->n_repairs);
+    d->n_dar = dar_emit(n, d->Nh, d->T, NULL);
     d->dar = (or_dar_entry *)malloc(sizeof(or_dar_entry) * (d->n_dar ? d->n_dar : 1));
-    dar_emit(n, d->T, d->dar);
+    dar_emit(n, d->Nh, d->T, d->dar);
     /* route time in minutes (Eq. (cost)): end of route minus departure */
     d->C = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
     d->Cc = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
@@ -307,6 +318,10 @@ or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int 
     or_day_set_theta(d, theta);
     if (err) *err = OR_OK;
     return d;
+}
+
+or_day *or_day_build(const or_net *n, const float *speed_mph, double theta, int *err) {
+    return or_day_build_coupled(n, speed_mph, NULL, theta, err);
 }
 
 void or_day_destroy(or_day *d) {
@@ -350,9 +365,9 @@ void or_day_get_B(const or_day *d, int32_t *row, int32_t *col, double *val) {
 /* xhat = B q, rows (h2, o) in the time-major order of Table "DODE framework */
 /* variable vectorization".                                                 */
 /* ------------------------------------------------------------------------ */
-void or_forward(const or_day *d, const double *q /* [N][K] */, double *xhat /* [N][O] */) {
+void or_forward(const or_day *d, const double *q /* [N][K] */, double *xhat /* [Nh][O] */) {
     const or_net *n = d->net;
-    memset(xhat, 0, sizeof(double) * (size_t)n->N * n->O);
+    memset(xhat, 0, sizeof(double) * (size_t)d->Nh * n->O);
     for (int64_t e = 0; e < d->nnz; ++e) xhat[d->b_row[e]] += d->b_val[e] * q[d->b_col[e]];
 }
 
@@ -369,7 +384,7 @@ double or_residual(const or_day *d, const double *xhat, const float *counts, con
 }
 
 /* Step 7 -- g = B^T r (Algorithm 1, gradient line, without the factor 2).   */
-void or_adjoint(const or_day *d, const double *r /* [N][O] */, double *g /* [N][K] */) {
+void or_adjoint(const or_day *d, const double *r /* [Nh][O] */, double *g /* [N][K] */) {
     const or_net *n = d->net;
     memset(g, 0, sizeof(double) * (size_t)n->N * n->K);
     for (int64_t e = 0; e < d->nnz; ++e) g[d->b_col[e]] += d->b_val[e] * r[d->b_row[e]];
@@ -563,11 +578,11 @@ double or_loss_grad_day(const or_day *d, const float *counts, const uint8_t *mas
     return loss;
 }
 
-/* Dense B (rows N*O, cols N*K) for tiny instances.                          */
+/* Dense B (rows Nh*O, cols N*K) for tiny instances.                         */
 void or_day_dense_B(const or_day *d, double *Bd) {
     const or_net *n = d->net;
     size_t cols = (size_t)n->N * n->K;
-    memset(Bd, 0, sizeof(double) * (size_t)n->N * n->O * cols);
+    memset(Bd, 0, sizeof(double) * (size_t)d->Nh * n->O * cols);
     for (int64_t e = 0; e < d->nnz; ++e) Bd[(size_t)d->b_row[e] * cols + d->b_col[e]] += d->b_val[e];
 }
 
@@ -628,4 +643,171 @@ int or_forward_days(const or_net *n, int32_t D, const float *speeds, const doubl
         or_day_destroy(d);
     }
     return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Consecutive days solved jointly.  Sec. 2.7 states the problem over the   */
+/* whole period as one NNLS and decomposes it into days, at the price of    */
+/* the vehicles that depart before midnight and arrive the next day.  Here  */
+/* the days stay coupled: day d's model is built with the next day's speeds */
+/* (Nh = 2N), so its B has rows [0, N) on day d and rows [N, 2N) on day     */
+/* d + 1.  With x_d = B_d q_d over the whole horizon:                        */
+/*   xhat_d = x_d[0, N) + x_{d-1}[N, 2N),   r_d = m_d (xhat_d - x_d),          */
+/*   loss_d = |r_d|^2,   g_d = B_d^T [r_d ; r_{d+1}]                           */
+/* (Algorithm 1's gradient, without the factor 2).  The last day keeps      */
+/* Nh = N: its mass after midnight is dropped as in the per-day problem.    */
+/* Algorithm 1 runs with full-row updates on all days at once: per epoch    */
+/* the forward of every day, then every day's Adagrad step and projection.  */
+/* Days [D][N][A] speeds, [D][N][O] counts / mask, q / G FP64 [D][N][K].     */
+/* ------------------------------------------------------------------------ */
+static or_day **or_build_coupled_days(const or_net *n, int32_t D, const float *speeds, double theta, int *status) {
+    const size_t sA = (size_t)n->N * n->A;
+    or_day **days = (or_day **)calloc((size_t)D, sizeof(or_day *));
+    *status = OR_OK;
+    for (int32_t i = 0; i < D; ++i) {
+        int err = OR_OK;
+        days[i] = or_day_build_coupled(n, speeds + sA * i, i + 1 < D ? speeds + sA * (i + 1) : NULL, theta, &err);
+        if (!days[i]) {
+            *status = err;
+            for (int32_t j = 0; j < i; ++j) or_day_destroy(days[j]);
+            free(days);
+            return NULL;
+        }
+    }
+    return days;
+}
+
+static void or_free_days(or_day **days, int32_t D) {
+    for (int32_t i = 0; i < D; ++i) or_day_destroy(days[i]);
+    free(days);
+}
+
+/* xhat [D][N][O] of the coupled days; xfull [D][2N][O] is scratch.           */
+static void or_forward_coupled_days(or_day **days, int32_t D, const double *q, double *xfull, double *xhat) {
+    const or_net *n = days[0]->net;
+    const size_t sO = (size_t)n->N * n->O, sK = (size_t)n->N * n->K;
+    for (int32_t i = 0; i < D; ++i) {
+        memset(xfull + 2 * sO * i, 0, sizeof(double) * 2 * sO);
+        or_forward(days[i], q + sK * i, xfull + 2 * sO * i);
+    }
+    for (int32_t i = 0; i < D; ++i)
+        for (size_t c = 0; c < sO; ++c)
+            xhat[sO * i + c] = xfull[2 * sO * i + c] + (i > 0 ? xfull[2 * sO * (i - 1) + sO + c] : 0.0);
+}
+
+int or_forward_coupled(const or_net *n, int32_t D, const float *speeds, const double *q, double theta,
+                       double *xhat) {
+    int status = OR_OK;
+    or_day **days = or_build_coupled_days(n, D, speeds, theta, &status);
+    if (!days) return status;
+    double *xfull = (double *)malloc(sizeof(double) * 2 * (size_t)n->N * n->O * D);
+    or_forward_coupled_days(days, D, q, xfull, xhat);
+    free(xfull);
+    or_free_days(days, D);
+    return OR_OK;
+}
+
+/* Residuals r [D][2N][O]: rows [0, N) of day d hold r_d, rows [N, 2N) hold  */
+/* r_{d+1} (zero for the last day).  Returns the per-day losses in loss.     */
+static void or_residual_coupled(const or_net *n, int32_t D, const double *xhat, const float *counts,
+                                const uint8_t *mask, double *r, double *loss) {
+    const size_t sO = (size_t)n->N * n->O;
+    for (int32_t i = 0; i < D; ++i) {
+        double l = 0.0;
+        for (size_t c = 0; c < sO; ++c) {
+            const double v = mask[sO * i + c] ? xhat[sO * i + c] - (double)counts[sO * i + c] : 0.0;
+            r[2 * sO * i + c] = v;
+            if (i > 0) r[2 * sO * (i - 1) + sO + c] = v;
+            l += v * v;
+        }
+        loss[i] = l;
+    }
+    memset(r + 2 * sO * (D - 1) + sO, 0, sizeof(double) * sO);
+}
+
+int or_solve_coupled(const or_net *n, int32_t D, const float *speeds, const float *counts, const uint8_t *mask,
+                     double theta, int32_t iters, double eta, double eps, double *q_inout, double *G_inout,
+                     double *loss_out, double *loss_trace /* [iters][D] or NULL */) {
+    int status = OR_OK;
+    or_day **days = or_build_coupled_days(n, D, speeds, theta, &status);
+    if (!days) return status;
+    const size_t sO = (size_t)n->N * n->O, sK = (size_t)n->N * n->K;
+    double *xfull = (double *)malloc(sizeof(double) * 2 * sO * D);
+    double *xhat = (double *)malloc(sizeof(double) * sO * D);
+    double *r = (double *)malloc(sizeof(double) * 2 * sO * D);
+    double *g = (double *)malloc(sizeof(double) * sK);
+    for (int32_t e = 0; e < iters; ++e) {
+        or_forward_coupled_days(days, D, q_inout, xfull, xhat);
+        or_residual_coupled(n, D, xhat, counts, mask, r, loss_out);
+        if (loss_trace) memcpy(loss_trace + (size_t)e * D, loss_out, sizeof(double) * D);
+        for (int32_t i = 0; i < D; ++i) {
+            or_adjoint(days[i], r + 2 * sO * i, g);
+            adagrad_project(sK, g, eta, eps, q_inout + sK * i, G_inout + sK * i);
+        }
+    }
+    or_forward_coupled_days(days, D, q_inout, xfull, xhat);
+    or_residual_coupled(n, D, xhat, counts, mask, r, loss_out);
+    free(xfull); free(xhat); free(r); free(g);
+    or_free_days(days, D);
+    return OR_OK;
+}
+
+/* Differentiable form of the coupled days: per-day loss, dL/dq = 2 g_d and  */
+/* dL/dtheta split by the day whose route choice it differentiates          */
+/* (dp_k/dtheta = p_k (-C_k + sum_{k' in od} p_k' C_k'), Eq. (logit)).         */
+int or_loss_grad_coupled(const or_net *n, int32_t D, const float *speeds, const float *counts,
+                         const uint8_t *mask, double theta, const double *q, double *loss, double *dq,
+                         double *dtheta) {
+    int status = OR_OK;
+    or_day **days = or_build_coupled_days(n, D, speeds, theta, &status);
+    if (!days) return status;
+    const size_t sO = (size_t)n->N * n->O, sK = (size_t)n->N * n->K;
+    double *xfull = (double *)malloc(sizeof(double) * 2 * sO * D);
+    double *xhat = (double *)malloc(sizeof(double) * sO * D);
+    double *r = (double *)malloc(sizeof(double) * 2 * sO * D);
+    or_forward_coupled_days(days, D, q, xfull, xhat);
+    or_residual_coupled(n, D, xhat, counts, mask, r, loss);
+    double *gp = (double *)malloc(sizeof(double) * (size_t)n->N * n->P);
+    for (int32_t i = 0; i < D; ++i) {
+        const or_day *d = days[i];
+        const double *ri = r + 2 * sO * i;
+        or_adjoint(d, ri, dq + sK * i);
+        for (size_t c = 0; c < sK; ++c) dq[sK * i + c] *= 2.0;
+        memset(gp, 0, sizeof(double) * (size_t)n->N * n->P);
+        for (int64_t e = 0; e < d->n_dar; ++e) {
+            const or_dar_entry *x = &d->dar[e];
+            int32_t o = n->obs_col[n->rlinks[n->rptr[x->k] + x->j]];
+            if (o < 0) continue;
+            gp[(size_t)x->h1 * n->P + x->k] += x->rho * ri[(size_t)x->h2 * n->O + o];
+        }
+        double acc = 0.0;
+        for (int32_t h = 0; h < n->N; ++h)
+            for (int32_t k = 0; k < n->P; ++k) {
+                const int32_t od = n->rod[k];
+                double mean_c = 0.0;
+                for (int32_t k2 = 0; k2 < n->P; ++k2)
+                    if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->Cc[(size_t)h * n->P + k2];
+                const double pk = d->p[(size_t)h * n->P + k];
+                acc += 2.0 * q[sK * i + (size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * pk *
+                       (-d->Cc[(size_t)h * n->P + k] + mean_c);
+            }
+        dtheta[i] = acc;
+    }
+    free(gp); free(xfull); free(xhat); free(r);
+    or_free_days(days, D);
+    return OR_OK;
+}
+
+/* Horizon (intervals) and DAR entries of day i of D coupled days (tests).   */
+int or_coupled_day_dar(const or_net *n, int32_t D, int32_t i, const float *speeds, int32_t *Nh, int64_t *n_dar,
+                       int32_t *kjh /* [n][4] or NULL */, double *rho /* or NULL */) {
+    const size_t sA = (size_t)n->N * n->A;
+    int err = OR_OK;
+    or_day *d = or_day_build_coupled(n, speeds + sA * i, i + 1 < D ? speeds + sA * (i + 1) : NULL, 0.0, &err);
+    if (!d) return err;
+    *Nh = d->Nh;
+    *n_dar = d->n_dar;
+    if (kjh && rho) or_day_get_dar(d, kjh, rho);
+    or_day_destroy(d);
+    return OR_OK;
 }

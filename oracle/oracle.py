@@ -73,6 +73,17 @@ def lib():
         L.or_forward_days.restype = ct.c_int
         L.or_forward_days.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, ct.c_int32,
                                       _f64p]
+        L.or_forward_coupled.restype = ct.c_int
+        L.or_forward_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, _f64p]
+        L.or_solve_coupled.restype = ct.c_int
+        L.or_solve_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, ct.c_int32,
+                                       ct.c_double, ct.c_double, _f64p, _f64p, _f64p, _f64p]
+        L.or_loss_grad_coupled.restype = ct.c_int
+        L.or_loss_grad_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, _f64p,
+                                           _f64p, _f64p, _f64p]
+        L.or_coupled_day_dar.restype = ct.c_int
+        L.or_coupled_day_dar.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _f32p, _i32p, _i64p, _i32p,
+                                         _f64p]
         _lib = L
     return _lib
 
@@ -150,6 +161,61 @@ class Net:
         if rc != 0:
             raise OracleError(f"or_forward_days rc={rc}")
         return x
+
+    # ---- consecutive days solved jointly (trips that cross midnight) ------
+    def forward_coupled(self, speeds, q, theta=0.1) -> np.ndarray:
+        """xhat [D][N][O] of D consecutive coupled days (or_solve_coupled)."""
+        D = speeds.shape[0]
+        sp, qq = _c(speeds, np.float32), _c(q, np.float64)
+        x = np.zeros((D, self.N, self.O))
+        rc = lib().or_forward_coupled(self.h, D, _p(sp, _f32p), _p(qq, _f64p), theta, _p(x, _f64p))
+        if rc != 0:
+            raise OracleError(f"or_forward_coupled rc={rc}")
+        return x
+
+    def solve_coupled(self, speeds, counts, mask, theta=0.1, iters=200, eta=5.0, eps=1e-10, q0=None, G0=None,
+                      trace=False):
+        """Algorithm 1 on the joint problem of D consecutive days; returns q, G,
+        the per-day final losses (and the [iters][D] pre-step loss trace)."""
+        D = speeds.shape[0]
+        sp, ct_, mk = _c(speeds, np.float32), _c(counts, np.float32), _c(mask, np.uint8)
+        q = np.zeros((D, self.N, self.K)) if q0 is None else _c(q0, np.float64).copy()
+        G = np.zeros((D, self.N, self.K)) if G0 is None else _c(G0, np.float64).copy()
+        loss = np.zeros(D)
+        tr = np.zeros((max(iters, 1), D))
+        rc = lib().or_solve_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta, iters, eta,
+                                    eps, _p(q, _f64p), _p(G, _f64p), _p(loss, _f64p),
+                                    _p(tr, _f64p) if trace else None)
+        if rc != 0:
+            raise OracleError(f"or_solve_coupled rc={rc}")
+        return (q, G, loss, tr[:iters]) if trace else (q, G, loss)
+
+    def loss_grad_coupled(self, speeds, counts, mask, q, theta=0.1):
+        """Per-day loss, dL/dq [D][N][K] and dL/dtheta per day of the coupled days."""
+        D = speeds.shape[0]
+        sp, ct_, mk, qq = _c(speeds, np.float32), _c(counts, np.float32), _c(mask, np.uint8), _c(q, np.float64)
+        loss, dth = np.zeros(D), np.zeros(D)
+        dq = np.zeros((D, self.N, self.K))
+        rc = lib().or_loss_grad_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta,
+                                        _p(qq, _f64p), _p(loss, _f64p), _p(dq, _f64p), _p(dth, _f64p))
+        if rc != 0:
+            raise OracleError(f"or_loss_grad_coupled rc={rc}")
+        return loss, dq, dth
+
+    def coupled_dar(self, speeds, i):
+        """Horizon Nh and DAR entries ([n][4] (k, j, h1, h2), rho) of day i of the
+        coupled days; h2 >= N lies on day i + 1."""
+        D = speeds.shape[0]
+        sp = _c(speeds, np.float32)
+        Nh, n = ct.c_int32(0), ct.c_int64(0)
+        rc = lib().or_coupled_day_dar(self.h, D, i, _p(sp, _f32p), ct.byref(Nh), ct.byref(n), None, None)
+        if rc != 0:
+            raise OracleError(f"or_coupled_day_dar rc={rc}")
+        kjh = np.zeros((n.value, 4), np.int32)
+        rho = np.zeros(n.value)
+        lib().or_coupled_day_dar(self.h, D, i, _p(sp, _f32p), ct.byref(Nh), ct.byref(n), _p(kjh, _i32p),
+                                 _p(rho, _f64p))
+        return Nh.value, kjh, rho
 
 
 class Day:
