@@ -434,6 +434,18 @@ def run_gpu(args):
         nxt["dar_distance"] = {"ms": ms_d, "days": D, "mean_dist": float(dist.mean()),
                                "rel_to_mean_norm": float(dist.mean() / np.sqrt(msq))}
         c3.close()
+        # consecutive days solved jointly (trips that cross midnight count on the
+        # next day): every epoch adds a halo pass over the first and last phases
+        c4 = dode.Context.from_workload(w, precision=prec, couple_days=1)
+        c4.use_torch_stream()
+        c4.set_days(ct_d, sp_d, mk_d)
+        c4.solve(1, args.step, args.batch, q_out=q_d, loss_out=l_d)           # warm-up
+        c4.set_days(ct_d, sp_d, mk_d)
+        c4.solve(args.compare_epochs, args.step, args.batch, q_out=q_d, loss_out=l_d)
+        kms = c4.last_kernel_ms()
+        nxt["coupled"] = {"day_iter_per_s": D * args.compare_epochs / (kms / 1e3), "epochs": args.compare_epochs,
+                          "launches": c4.last_launches(), "final_loss": float(l_d.double().sum().item())}
+        c4.close()
         # the paper's efficiency experiment at its largest size: dense random
         # n x n NNLS by Algorithm 1, one pass over B (4 n^2 bytes) per iteration
         n = args.dense_n

@@ -113,6 +113,19 @@ typedef struct {
     int32_t max_ctas;        /* cap on resident CTAs of the fused kernel (0 = as many as fit) */
     int32_t day_base;        /* index of the first loaded day in the caller's day numbering (>= 0);
                                 seeds the row permutation of row_chunk > 0 */
+    int32_t couple_days;     /* 1: the loaded days are consecutive and are solved jointly -- the
+                                whole-period NNLS of Sec. 2.7 without its cut at midnight.  A trip
+                                that departs on day d and is still travelling after midnight takes
+                                day d + 1's link times and counts on day d + 1's links (its first
+                                maxoff + 2 intervals); the gradient of day d's demand then includes
+                                day d + 1's residuals.  The last loaded day drops mass after its
+                                midnight as the per-day problem does.  Needs the fused form,
+                                row_chunk = 0 and a network whose accumulator ring and tick window
+                                fit in shared memory (else DODE_ERR_UNSUPPORTED at the first
+                                evaluation).  Each epoch then takes two launches; use_graph is
+                                ignored.  dode_dar_distance, dode_get_dar and
+                                dode_loss_static_scratch refuse coupled days.  0 = independent
+                                days (default). */
 } dode_options;
 
 typedef struct dode_ctx dode_ctx;

@@ -757,7 +757,7 @@ int or_solve_coupled(const or_net *n, int32_t D, const float *speeds, const floa
 /* (dp_k/dtheta = p_k (-C_k + sum_{k' in od} p_k' C_k'), Eq. (logit)).         */
 int or_loss_grad_coupled(const or_net *n, int32_t D, const float *speeds, const float *counts,
                          const uint8_t *mask, double theta, const double *q, double *loss, double *dq,
-                         double *dtheta) {
+                         double *dtheta, double *dtheta_abs /* per day sum of |terms|, or NULL */) {
     int status = OR_OK;
     or_day **days = or_build_coupled_days(n, D, speeds, theta, &status);
     if (!days) return status;
@@ -780,7 +780,7 @@ int or_loss_grad_coupled(const or_net *n, int32_t D, const float *speeds, const 
             if (o < 0) continue;
             gp[(size_t)x->h1 * n->P + x->k] += x->rho * ri[(size_t)x->h2 * n->O + o];
         }
-        double acc = 0.0;
+        double acc = 0.0, acc_abs = 0.0;
         for (int32_t h = 0; h < n->N; ++h)
             for (int32_t k = 0; k < n->P; ++k) {
                 const int32_t od = n->rod[k];
@@ -788,10 +788,13 @@ int or_loss_grad_coupled(const or_net *n, int32_t D, const float *speeds, const 
                 for (int32_t k2 = 0; k2 < n->P; ++k2)
                     if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->Cc[(size_t)h * n->P + k2];
                 const double pk = d->p[(size_t)h * n->P + k];
-                acc += 2.0 * q[sK * i + (size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * pk *
-                       (-d->Cc[(size_t)h * n->P + k] + mean_c);
+                const double term = 2.0 * q[sK * i + (size_t)h * n->K + od] * gp[(size_t)h * n->P + k] * pk *
+                                    (-d->Cc[(size_t)h * n->P + k] + mean_c);
+                acc += term;
+                acc_abs += fabs(term);
             }
         dtheta[i] = acc;
+        if (dtheta_abs) dtheta_abs[i] = acc_abs;
     }
     free(gp); free(xfull); free(xhat); free(r);
     or_free_days(days, D);

@@ -80,7 +80,7 @@ def lib():
                                        ct.c_double, ct.c_double, _f64p, _f64p, _f64p, _f64p]
         L.or_loss_grad_coupled.restype = ct.c_int
         L.or_loss_grad_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, _f64p,
-                                           _f64p, _f64p, _f64p]
+                                           _f64p, _f64p, _f64p, _f64p]
         L.or_coupled_day_dar.restype = ct.c_int
         L.or_coupled_day_dar.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _f32p, _i32p, _i64p, _i32p,
                                          _f64p]
@@ -190,17 +190,19 @@ class Net:
             raise OracleError(f"or_solve_coupled rc={rc}")
         return (q, G, loss, tr[:iters]) if trace else (q, G, loss)
 
-    def loss_grad_coupled(self, speeds, counts, mask, q, theta=0.1):
-        """Per-day loss, dL/dq [D][N][K] and dL/dtheta per day of the coupled days."""
+    def loss_grad_coupled(self, speeds, counts, mask, q, theta=0.1, with_scale=False):
+        """Per-day loss, dL/dq [D][N][K] and dL/dtheta per day of the coupled days
+        (with_scale: also each day's sum of |dL/dtheta terms|)."""
         D = speeds.shape[0]
         sp, ct_, mk, qq = _c(speeds, np.float32), _c(counts, np.float32), _c(mask, np.uint8), _c(q, np.float64)
-        loss, dth = np.zeros(D), np.zeros(D)
+        loss, dth, dabs = np.zeros(D), np.zeros(D), np.zeros(D)
         dq = np.zeros((D, self.N, self.K))
         rc = lib().or_loss_grad_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta,
-                                        _p(qq, _f64p), _p(loss, _f64p), _p(dq, _f64p), _p(dth, _f64p))
+                                        _p(qq, _f64p), _p(loss, _f64p), _p(dq, _f64p), _p(dth, _f64p),
+                                        _p(dabs, _f64p))
         if rc != 0:
             raise OracleError(f"or_loss_grad_coupled rc={rc}")
-        return loss, dq, dth
+        return (loss, dq, dth, dabs) if with_scale else (loss, dq, dth)
 
     def coupled_dar(self, speeds, i):
         """Horizon Nh and DAR entries ([n][4] (k, j, h1, h2), rho) of day i of the

@@ -65,6 +65,9 @@ struct dode_ctx {
     std::vector<unsigned long long> h_repairs;
     int maxoff_max = 0;
     int max_tick = 0;
+    // coupled days: early / halo rows of every day (MODE_HALO output)
+    long long *d_early = nullptr, *d_halo = nullptr;
+    int halo_rows = 0;
     float *d_q = nullptr, *d_G = nullptr, *d_qtmp = nullptr, *d_gout = nullptr, *d_xout = nullptr;
     __nv_bfloat16 *d_qb = nullptr;
     double *d_loss = nullptr, *d_dtheta = nullptr;
@@ -311,6 +314,9 @@ int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
     }
     if (smem > budget + reserve)
         return fail(ctx, DODE_ERR_UNSUPPORTED, "route tables of this network do not fit in shared memory");
+    if (ctx->opt.couple_days && (R == 0 || RW == 0))
+        return fail(ctx, DODE_ERR_UNSUPPORTED,
+                    "couple_days needs the accumulator ring and the tick window in shared memory");
     int occ = 0;
     cudaError_t e = fused_occupancy(precision, block, smem, &occ);
     if (e != cudaSuccess) return fail(ctx, DODE_ERR_CUDA, std::string("occupancy: ") + cudaGetErrorString(e));
@@ -554,6 +560,12 @@ FusedParams base_params(dode_ctx *ctx) {
     p.row_chunk = 0;
     p.seed = ctx->opt.seed;
     p.day_base = ctx->opt.day_base;
+    p.coupled = ctx->opt.couple_days;
+    p.halo_rows = ctx->halo_rows;
+    p.Nh = ctx->N + (ctx->opt.couple_days ? ctx->halo_rows : 0);
+    p.early = ctx->d_early;
+    p.halo = ctx->d_halo;
+    p.no_final = 0;
     return p;
 }
 
@@ -566,11 +578,53 @@ int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
     slot_params(ctx, s, &p);
     CUL(launch_route_choice(choice_C(ctx), ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, ctx->D, ctx->P, ctx->N,
                             ctx->Np, ctx->d_pt, ctx->stream));
-    CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    ctx->last_launches = 1;
+    if (p.coupled) {
+        // coupled days: every day's early rows and spill for this q first
+        FusedParams ph = p;
+        ph.mode = MODE_HALO;
+        CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
+        CUL(launch_fused(ph, precision, s.grid, s.block, s.smem, ctx->stream));
+        ++ctx->last_launches;
+    }
+    CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
     CUL(launch_fused(p, precision, s.grid, s.block, s.smem, ctx->stream));
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
-    ctx->last_launches = 1;
+    return DODE_OK;
+}
+
+// Coupled days (consecutive days solved jointly): Algorithm 1 with full-row
+// updates on the joint problem.  Every epoch is a halo pass (each day's own
+// deposits into its first rows and its spill past midnight, for the current
+// q) and a one-epoch solve pass that adds the previous day's spill to each
+// day's first rows and gathers the next day's first residual rows in the
+// adjoint; the final loss is one more halo pass and a forward.
+int solve_coupled(dode_ctx *ctx, FusedParams p, int iters) {
+    const int prec = ctx->opt.precision;
+    FusedShape s;
+    int rc = fused_shape(ctx, prec, &s);
+    if (rc) return rc;
+    rc = ensure_slots(ctx, s, prec);
+    if (rc) return rc;
+    slot_params(ctx, s, &p);
+    CUL(launch_route_choice(choice_C(ctx), ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, ctx->D, ctx->P, ctx->N,
+                            ctx->Np, ctx->d_pt, ctx->stream));
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    FusedParams ph = p;
+    ph.mode = MODE_HALO;
+    for (int it = 0; it <= iters; ++it) {
+        CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
+        CUL(launch_fused(ph, prec, s.grid, s.block, s.smem, ctx->stream));
+        FusedParams ps = p;
+        ps.iters = it < iters ? 1 : 0;                  // the last pass: forward and final loss only
+        ps.no_final = it < iters ? 1 : 0;
+        ps.trace = (it < iters && p.trace) ? p.trace + (size_t)it * ctx->D : nullptr;
+        CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
+        CUL(launch_fused(ps, prec, s.grid, s.block, s.smem, ctx->stream));
+    }
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    ctx->last_launches = 2LL * (iters + 1);
     return DODE_OK;
 }
 
@@ -611,6 +665,9 @@ void free_days(dode_ctx *ctx) {
     dfree(ctx->d_xout);
     dfree(ctx->d_loss);
     dfree(ctx->d_dtheta);
+    dfree(ctx->d_early);
+    dfree(ctx->d_halo);
+    ctx->halo_rows = 0;
     dfree(ctx->d_trace);
     ctx->trace_cap = 0;
     dfree(ctx->d_rec);
@@ -799,8 +856,11 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     if (o.n_intervals < 1 || o.interval_s < 1 || o.ticks_per_s < 1 || !std::isfinite(o.theta_per_min) ||
         !(o.eps >= 0.f) || o.row_chunk < 0 || (o.form != DODE_FORM_FUSED && o.form != DODE_FORM_PLAIN) ||
         (o.precision != DODE_PREC_FP32 && o.precision != DODE_PREC_BF16) || o.block_threads < 0 || o.ctas_per_sm < 0 ||
-        o.max_ctas < 0 || (o.use_graph != 0 && o.use_graph != 1) || o.day_base < 0)
+        o.max_ctas < 0 || (o.use_graph != 0 && o.use_graph != 1) || o.day_base < 0 ||
+        (o.couple_days != 0 && o.couple_days != 1))
         return bail(DODE_ERR_ARG, "options");
+    if (o.couple_days && (o.form != DODE_FORM_FUSED || o.row_chunk > 0))
+        return bail(DODE_ERR_ARG, "couple_days needs the fused form with full-row updates (row_chunk = 0)");
     if (o.row_chunk > 0 && (long long)o.n_intervals * net->n_obs >= (1LL << 31))
         return bail(DODE_ERR_ARG, "row_chunk > 0 needs n_intervals * n_obs < 2^31 row ids");
     const long long ipt = (long long)o.interval_s * o.ticks_per_s;
@@ -1073,6 +1133,7 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
     pp.tab_off = ctx->d_tab_off;
     pp.traj_tab = nullptr;
     pp.n_days = D;
+    pp.coupled = ctx->opt.couple_days;
     CUL(launch_prepare(pp, ctx->stream));
     ctx->h_maxoff.resize(D);
     ctx->h_repairs.resize(D);
@@ -1081,6 +1142,16 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
                        ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->maxoff_max = *std::max_element(ctx->h_maxoff.begin(), ctx->h_maxoff.end());
+    if (ctx->opt.couple_days) {
+        // rows of the next day that a day's trips reach: every arrival row is at
+        // most maxoff + 1 past its departure row
+        dfree(ctx->d_early);
+        dfree(ctx->d_halo);
+        ctx->halo_rows = ctx->maxoff_max + 2;
+        const size_t nh = (size_t)D * ctx->O * ctx->halo_rows;
+        CU(dalloc(&ctx->d_early, nh));
+        CU(dalloc(&ctx->d_halo, nh));
+    }
     // pass 2 for days that needed FIFO repairs: keep their exact trajectories
     std::vector<int64_t> off(D, -1);
     const size_t per_day = (size_t)(ctx->L + ctx->P) * (N + 1);
@@ -1212,7 +1283,12 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
         p.iters = iters;
         p.eta = step;
         p.trace = iters > 0 ? ctx->d_trace : nullptr;
-        if (ctx->opt.use_graph && ptr_kind == DODE_PTR_DEVICE) {
+        if (ctx->opt.couple_days) {
+            if (ctx->opt.precision == DODE_PREC_BF16)
+                CUL(launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, ctx->stream));
+            rc = solve_coupled(ctx, p, iters);
+            if (rc) return rc;
+        } else if (ctx->opt.use_graph && ptr_kind == DODE_PTR_DEVICE) {
             rc = solve_graph(ctx, p, iters, step, q_out, loss_out);
             if (rc) return rc;
             ctx->trace_iters = iters;
@@ -1223,10 +1299,12 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
             CU(cudaStreamSynchronize(ctx->stream));
             return DODE_OK;
         }
-        if (ctx->opt.precision == DODE_PREC_BF16)
-            CUL(launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, ctx->stream));
-        rc = run_fused(ctx, p, ctx->opt.precision);
-        if (rc) return rc;
+        if (!ctx->opt.couple_days) {
+            if (ctx->opt.precision == DODE_PREC_BF16)
+                CUL(launch_to_bf16(ctx->d_q, ctx->d_qb, (size_t)D * ctx->K * ctx->Np, ctx->stream));
+            rc = run_fused(ctx, p, ctx->opt.precision);
+            if (rc) return rc;
+        }
     }
     ctx->trace_iters = iters;
     rc = finish_timing(ctx);
@@ -1501,6 +1579,7 @@ int dode_r2(dode_ctx *ctx, const float *q, float theta, double *r2, int32_t ptr_
 int dode_dar_distance(dode_ctx *ctx, double *dist, double *mean_sq) {
     if (!ctx) return DODE_ERR_ARG;
     if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
+    if (ctx->opt.couple_days) return fail(ctx, DODE_ERR_UNSUPPORTED, "dar_distance compares per-day DARs (couple_days = 0)");
     if (!dist) return fail(ctx, DODE_ERR_ARG, "dar_distance arguments");
     int rc = set_device(ctx);
     if (rc) return rc;
@@ -1593,6 +1672,7 @@ int dode_get_day_info(dode_ctx *ctx, int32_t day, int64_t *n_repairs, int32_t *m
 int dode_get_dar(dode_ctx *ctx, int32_t day, int64_t *n, int32_t *kjh, float *rho) {
     if (!ctx || !n) return DODE_ERR_ARG;
     if (day < 0 || day >= ctx->D) return fail(ctx, DODE_ERR_ARG, "day out of range");
+    if (ctx->opt.couple_days) return fail(ctx, DODE_ERR_UNSUPPORTED, "get_dar lists per-day DARs (couple_days = 0)");
     int rc = set_device(ctx);
     if (rc) return rc;
     // every (route, position) pair, not only observed links
@@ -1719,6 +1799,7 @@ extern "C" int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float the
     if (!ctx) return DODE_ERR_ARG;
     if (ctx->D == 0) return fail(ctx, DODE_ERR_STATE, "no days loaded");
     if (!q || !loss || !std::isfinite(theta)) return fail(ctx, DODE_ERR_ARG, "loss_static_scratch arguments");
+    if (ctx->opt.couple_days) return fail(ctx, DODE_ERR_UNSUPPORTED, "loss_static_scratch takes independent days");
     int rc = set_device(ctx);
     if (rc) return rc;
     unsigned char *base = nullptr;

@@ -27,7 +27,9 @@ constexpr int kMaxRouteLinks = 64;
 constexpr int kGroupRoutes = 32;      // routes per walk group of the fused kernel
 constexpr int kRankBins = 4096;       // row-chunk ranking: bins on the keys' top 12 bits
 
-enum Mode : int { MODE_SOLVE = 0, MODE_FORWARD = 1, MODE_LOSS = 2, MODE_LOSS_GRAD = 3 };
+// MODE_HALO (coupled days): forward sweep only, writing each day's own deposits
+// into its first halo_rows rows (early) and its deposits past midnight (halo).
+enum Mode : int { MODE_SOLVE = 0, MODE_FORWARD = 1, MODE_LOSS = 2, MODE_LOSS_GRAD = 3, MODE_HALO = 4 };
 
 // floor(t / ipt) for 0 <= t < 2^31 via a 32-bit magic multiplier:
 // with l = ceil(log2 ipt) and M = ceil(2^(31+l) / ipt) < 2^32,
@@ -122,6 +124,13 @@ struct FusedParams {
     uint32_t *rc_bins;         // [grid][3][kRankBins] key-bin counts, first ranks, fill cursors
     unsigned long long *rc_key;  // [grid][O N] keys of the rows in bins that straddle a chunk boundary
     int32_t *rc_row;           // [grid][O N] their row ids
+    // consecutive days solved jointly (trips that cross midnight reach the next day)
+    int coupled;
+    int halo_rows;             // S: rows of the next day that a day's trips reach
+    int Nh;                    // deposit / gather horizon in rows: N, or N + S when coupled
+    long long *early;          // [D][O][S] own deposits into the day's rows [0, S), 2^-20 vehicles
+    long long *halo;           // [D][O][S] deposits into the next day's rows [0, S)
+    int no_final;              // SOLVE: stop after the last step, no final forward
 };
 
 struct PrepParams {
@@ -135,6 +144,7 @@ struct PrepParams {
     const int64_t *tab_off;    // [D] or null (pass 1)
     int32_t *traj_tab;
     int n_days;
+    int coupled;               // entries past midnight take the next day's link times
 };
 
 struct PlainParams {

@@ -264,7 +264,7 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
                                                int T, bool vw, const ST *S, int t, int E, int *stk) {
     const int lane = threadIdx.x & 31;
-    const int ipt = p.div.ipt, N = p.N;
+    const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     uint32_t Wu = (uint32_t)(S[E + 1] - S[t]);
     float Wf = __uint2float_rn(Wu);
     for (int j = j0; j < beta; ++j) {
@@ -316,7 +316,7 @@ template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
 __device__ __forceinline__ void forward_walk_f(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
                                                int T, bool vw, const long long *S, int t, int E, int *stk) {
-    const int ipt = p.div.ipt, N = p.N;
+    const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     float f = (float)((double)(S[E + 1] - S[t]) * kFxInv);
     for (int j = j0; j < beta; ++j) {
         const bool first32 = !LONG || j < 32;
@@ -444,7 +444,7 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
                                                 const uint32_t *SA, const uint32_t *SB, int t, int E, int *stkA,
                                                 int *stkB) {
     const int lane = threadIdx.x & 31;
-    const int ipt = p.div.ipt, N = p.N;
+    const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     uint32_t WuA = SA[E + 1] - SA[t], WuB = SB[E + 1] - SB[t];
     float WfA = __uint2float_rn(WuA), WfB = __uint2float_rn(WuB);
     for (int j = j0; j < beta; ++j) {
@@ -607,7 +607,7 @@ template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
 __device__ __forceinline__ float adjoint_walk(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                               const int32_t *trow, const RouteRegs &rr, const void *rb, int j0,
                                               int beta, int T, float G, bool vw, int *stk, float *gstk) {
-    const int ipt = p.div.ipt, N = p.N;
+    const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
     for (int j = j0; j < beta; ++j) {
         const bool first32 = !LONG || j < 32;
@@ -698,7 +698,7 @@ __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared
                                               const int32_t *trowA, const int32_t *trowB, const RouteRegs &rr,
                                               const void *rb, int j0, int beta, int TA, int TB, float &GA, float &GB,
                                               bool vwA, bool vwB, int *stkA, int *stkB, float *gstkA, float *gstkB) {
-    const int ipt = p.div.ipt, N = p.N;
+    const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
     for (int j = j0; j < beta; ++j) {
         const int tb = __shfl_sync(0xffffffffu, rr.t0, j & 31);
@@ -848,10 +848,13 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 
 // Tick rows [pb, pb + RW) of every link from the 16-bit table, whose entries
 // past the end of the day repeat the last interval (the link entry rule clamps
-// to it).  16-byte loads of 8 ticks at 8-aligned row positions, four per
-// thread in flight before the shared stores; chunks past the table row take
-// the last interval's value.
-__device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, const uint16_t *t16) {
+// to it), or, for coupled days (t16n = the next day's table), continue with
+// the next day's rows.  16-byte loads of 8 ticks at 8-aligned row positions,
+// four per thread in flight before the shared stores; chunks past the table
+// row take the last interval's value, chunks that reach past midnight of a
+// coupled day are gathered tick by tick.
+__device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, const uint16_t *t16,
+                                            const uint16_t *t16n) {
     const int c0 = s.pb & ~7;
     const int nch = (s.pb + s.RW - c0 + 7) >> 3;       // 8-tick chunks per link
     const int total = p.A * nch;
@@ -864,8 +867,18 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
             if (i < total) {
                 const int a = i / nch, c = c0 + 8 * (i - a * nch);
                 const uint16_t *row = t16 + (size_t)a * p.Np;
-                if (c + 8 <= p.Np) {
+                if (c + 8 <= (t16n ? p.N : p.Np)) {
                     v[u] = __ldg(reinterpret_cast<const uint4 *>(row + c));
+                } else if (t16n) {
+                    const uint16_t *nrow = t16n + (size_t)a * p.Np;
+                    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int x = c + k;
+                        const uint32_t t = x < p.N ? __ldg(row + x) : __ldg(nrow + min(x - p.N, p.N - 1));
+                        w[k >> 1] |= t << ((k & 1) * 16);
+                    }
+                    v[u] = make_uint4(w[0], w[1], w[2], w[3]);
                 } else {
                     uint32_t x = __ldg(row + p.Np - 1);
                     x |= x << 16;
@@ -890,12 +903,34 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
     }
 }
 
-// Residual rows [pb, pb + R) of every observed link, as float bits in the
-// accumulator array (rows past the end of the day are zero): 16-byte loads
-// (8 BF16 or 4 FP32 residuals) at aligned row positions, four per thread in
-// flight.
+// Residual of row r of the next day, seen from a coupled day: the next day's
+// own deposits into its first rows (early) plus this day's spill into them
+// (halo), turned into r = m (xhat - x) exactly as the next day's own flush
+// does it (EXACT: FP64, else the solve path's FP32), in the residual slot's
+// precision.
 template <int PREC>
-__device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, const void *rb) {
+__device__ __forceinline__ uint32_t next_day_residual(const FusedParams &p, int day, int o, int r, bool exact) {
+    const size_t S = (size_t)p.halo_rows, nc = (size_t)(day + 1) * p.O + o;
+    const long long v = p.early[nc * S + r] + p.halo[((size_t)day * p.O + o) * S + r];
+    const bool on = (__ldg(&p.mask[nc * p.Nw + (r >> 5)]) >> (r & 31)) & 1u;
+    const float c = __ldg(&p.counts[nc * p.Np + r]);
+    float rr;
+    if (exact) {
+        rr = on ? (float)((double)v * kFxInv - (double)c) : 0.f;
+    } else {
+        const float x = fmaf((float)(int)(v >> 32), 4096.f, __uint2float_rn((uint32_t)v) * 9.5367431640625e-7f);
+        rr = on ? x - c : 0.f;
+    }
+    return __float_as_uint(PREC == 1 ? bf16_round(rr) : rr);
+}
+
+// Residual rows [pb, pb + R) of every observed link, as float bits in the
+// accumulator array (rows past the end of the day are zero, or the next day's
+// residuals for a coupled day): 16-byte loads (8 BF16 or 4 FP32 residuals) at
+// aligned row positions, four per thread in flight.
+template <int PREC>
+__device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, const void *rb, int day,
+                                               bool exact) {
     constexpr int E = PREC == 1 ? 8 : 4;              // residuals per 16 bytes
     const int rows = min(s.R, p.N - s.pb);
     const int c0 = s.pb & ~(E - 1);
@@ -929,11 +964,16 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
             }
         }
     }
-    // rows past the end of the day gather nothing
+    // rows past the end of the day gather nothing, except the first rows of a
+    // coupled next day
     const int tail = s.R - rows;
+    const bool next = p.coupled && day + 1 < p.n_days;
     for (int i = threadIdx.x; i < p.O * tail; i += blockDim.x) {
-        const int o = i / tail;
-        s.lo[o * s.R + rows + (i - o * tail)] = 0u;
+        const int o = i / tail, x = rows + (i - o * tail);
+        const int r = s.pb + x - p.N;          // row of the next day (rows past its end: dropped)
+        uint32_t bits = 0u;
+        if (next && r >= 0 && r < min(p.halo_rows, p.N)) bits = next_day_residual<PREC>(p, day, o, r, exact);
+        s.lo[o * s.R + x] = bits;
     }
 }
 
@@ -1267,14 +1307,21 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         __syncthreads();
         const int day = s_day;
         if (day >= p.n_days) break;
-        for (int i = threadIdx.x; i < p.Ow; i += nthr) colact[i] = p.colact[(size_t)day * p.Ow + i];
+        const bool has_next = p.coupled && day + 1 < p.n_days;
+        // a coupled day also deposits on the next day's observed links (its trips
+        // that cross midnight)
+        for (int i = threadIdx.x; i < p.Ow; i += nthr)
+            colact[i] = p.colact[(size_t)day * p.Ow + i] | (has_next ? p.colact[(size_t)(day + 1) * p.Ow + i] : 0u);
         const int64_t toff = p.tab_off[day];
         const int32_t *tab = toff >= 0 ? p.traj_tab + toff : nullptr;
         const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
         const uint16_t *tick16_day = p.ticks16 + (size_t)day * p.A * p.Np;
+        const uint16_t *tick16_next = has_next ? tick16_day + (size_t)p.A * p.Np : nullptr;
         const float *cnt = p.counts + (size_t)day * p.O * p.Np;
         const uint32_t *mk = p.mask + (size_t)day * p.O * p.Nw;
-        const int maxoff = p.maxoff[day];
+        // coupled days: every day keeps the context's largest offset, so that the
+        // rows carried between phases always cover the halo rows
+        const int maxoff = p.coupled ? p.halo_rows - 2 : p.maxoff[day];
         // tiles per phase: the accumulators must hold a phase's arrival rows
         // (31 F + maxoff + 2) and the tick window its trajectories' entry rows
         // (31 F + maxoff + 1)
@@ -1302,15 +1349,35 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             // ------------------------------ forward sweep ------------------------------
             double lsum = 0.0;     // EXACT calls: FP64 (finite differences of the loss resolve tiny changes)
             float ks = 0.f, kc = 0.f;  // solve: compensated FP32 sum
+            const bool halo_pass = p.mode == MODE_HALO;
+            if (SMEM_RING && p.coupled && day > 0 && !halo_pass) {
+                // the previous day's trips that cross midnight: its deposits into
+                // this day's first rows go in first (the ring is clear here)
+                const long long *hin = p.halo + (size_t)(day - 1) * p.O * p.halo_rows;
+                for (int i = threadIdx.x; i < p.O * p.halo_rows; i += nthr) {
+                    const int o = i / p.halo_rows, r = i - o * p.halo_rows;
+                    const long long v = hin[i];
+                    s.lo[o * s.R + r] = (uint32_t)v;
+                    const int hw = (int)(v >> 32);
+                    if (hw) {
+                        s.hi[o * s.R + r] = hw;
+                        s_carry = 1;
+                    }
+                }
+                __syncthreads();
+            }
             for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
                 const int ntask = phase_tasks(nt, nbg, p.n_groups);
+                const int span = nt * kTileW;
+                // halo pass: only the phases that reach the first rows or midnight
+                const bool walk = !halo_pass || pb0 < p.halo_rows || pb0 + span + maxoff + 2 > p.N;
                 s.pb = pb0;
-                if (SMEM_TICKS && !tab) {
-                    stage_ticks(p, s, tick16_day);
+                if (walk && SMEM_TICKS && !tab) {
+                    stage_ticks(p, s, tick16_day, tick16_next);
                     __syncthreads();
                 }
-                while (true) {
+                while (walk) {
                     int t = 0;
                     if (lane == 0) t = atomicAdd(&s_task, 1);
                     t = __shfl_sync(0xffffffffu, t, 0);
@@ -1331,10 +1398,26 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 __syncthreads();
                 // rows [pb0, pb0 + 31 nt) are final: residual, loss, residual slot;
                 // the spill rows move to the front for the next phase
-                const int span = nt * kTileW;
                 const int rows = min(span, p.N - pb0);
                 const bool carry = s_carry != 0;
-                if (exact)
+                if (halo_pass) {
+                    if (SMEM_RING) {
+                        const int S = p.halo_rows;
+                        long long *early = p.early + (size_t)day * p.O * S;
+                        long long *halo = p.halo + (size_t)day * p.O * S;
+                        const int ne = pb0 < S ? min(rows, S - pb0) : 0;       // final rows of [0, S)
+                        for (int i = threadIdx.x; i < p.O * ne; i += nthr) {
+                            const int o = i / ne, r = i - o * ne, idx = o * s.R + r;
+                            early[o * S + pb0 + r] = ((long long)(carry ? s.hi[idx] : 0) << 32) | (long long)s.lo[idx];
+                        }
+                        if (pb0 + span >= p.N) {                                // the day's last phase
+                            for (int i = threadIdx.x; i < p.O * S; i += nthr) {
+                                const int o = i / S, r = i - o * S, idx = o * s.R + (p.N - pb0) + r;
+                                halo[i] = ((long long)(carry ? s.hi[idx] : 0) << 32) | (long long)s.lo[idx];
+                            }
+                        }
+                    }
+                } else if (exact)
                     flush_phase<PREC, SMEM_RING, true>(p, s, gacc, rb, cnt, mk, lab, sel, day, pb0, rows, carry, lsum,
                                                        ks, kc);
                 else
@@ -1382,9 +1465,10 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             const double loss_day = block_sum(exact ? lsum : (double)ks - (double)kc, s_red);
             if (threadIdx.x == 0 && chunk == 0) {
                 if (p.mode == MODE_SOLVE && it < p.iters && p.trace) p.trace[(size_t)it * p.n_days + day] = (float)loss_day;
-                if (p.mode != MODE_SOLVE || it == p.iters) p.loss[day] = loss_day;
+                if (!halo_pass && (p.mode != MODE_SOLVE || it == p.iters)) p.loss[day] = loss_day;
             }
-            if (p.mode == MODE_FORWARD || p.mode == MODE_LOSS || (p.mode == MODE_SOLVE && it >= p.iters)) break;
+            if (p.mode == MODE_FORWARD || p.mode == MODE_LOSS || halo_pass || (p.mode == MODE_SOLVE && it >= p.iters))
+                break;
             if (chunked && nch == 0) {      // no observed row: the epoch makes no update
                 ++it;
                 continue;
@@ -1396,8 +1480,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 const int ntask = phase_tasks(nt, nbg, p.n_groups);
                 s.pb = pb0;
                 __syncthreads();                           // previous phase done with the windows
-                if (SMEM_TICKS && !tab) stage_ticks(p, s, tick16_day);
-                if (SMEM_RING) stage_residual<PREC>(p, s, rb);
+                if (SMEM_TICKS && !tab) stage_ticks(p, s, tick16_day, tick16_next);
+                if (SMEM_RING) stage_residual<PREC>(p, s, rb, day, exact);
                 __syncthreads();
                 while (true) {
                     int t = 0;
@@ -1433,6 +1517,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             if (chunked && ++chunk < nch) continue;
             chunk = 0;
             ++it;
+            if (p.no_final && it >= p.iters) break;        // the caller takes the final loss
         }
     }
 }

@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(256) k_prepare(const PrepParams p) {
     const int day = (int)(gw / p.P), k = (int)(gw % p.P);
     const int l0 = p.rptr[k], l1 = p.rptr[k + 1], beta = l1 - l0;
     const int32_t *tk = p.ticks + (size_t)day * p.A * p.Np;
+    // coupled days: a link entered after midnight takes the next day's link time
+    const int32_t *tk_next = (p.coupled && day + 1 < p.n_days) ? tk + (size_t)p.A * p.Np : nullptr;
     const int ipt = p.div.ipt;
     int32_t *tab = nullptr;
     if (p.tab_off && p.tab_off[day] >= 0) tab = p.traj_tab + p.tab_off[day] + (size_t)(l0 + k) * (p.N + 1);
@@ -112,8 +114,13 @@ __global__ void __launch_bounds__(256) k_prepare(const PrepParams p) {
             const int a = p.rlinks[l0 + j];
             int raw = INT_MAX;
             if (valid) {
-                const int h = min(interval_of(T, p.div), p.N - 1);
-                raw = T + tk[(size_t)a * p.Np + h];
+                const int h = interval_of(T, p.div);
+                if (h < p.N)
+                    raw = T + tk[(size_t)a * p.Np + h];
+                else if (tk_next)
+                    raw = T + tk_next[(size_t)a * p.Np + min(h - p.N, p.N - 1)];
+                else
+                    raw = T + tk[(size_t)a * p.Np + p.N - 1];
             }
             // inclusive running max over lanes, seeded with the previous chunk
             int v = raw;

@@ -58,7 +58,7 @@ class dode_options(ct.Structure):
                 ("seed", ct.c_uint64), ("form", ct.c_int32), ("precision", ct.c_int32),
                 ("block_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32), ("device", ct.c_int32),
                 ("stream", ct.c_void_p), ("use_graph", ct.c_int32), ("max_ctas", ct.c_int32),
-                ("day_base", ct.c_int32)]
+                ("day_base", ct.c_int32), ("couple_days", ct.c_int32)]
 
 
 _lib = None

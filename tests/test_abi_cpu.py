@@ -33,6 +33,7 @@ def test_default_options(lib):
     assert o.theta_per_min == pytest.approx(0.1)
     assert o.eps == pytest.approx(1e-10)
     assert o.form == dode.FORM_FUSED and o.precision == dode.PREC_FP32
+    assert o.couple_days == 0 and o.day_base == 0
 
 
 def _ctx_args(w):
