@@ -57,7 +57,7 @@ def test_dense_spgd_device_pointers_and_errors():
     assert e.value.code == dode.ERR_ARG
 
 
-@pytest.mark.parametrize("nr,nc", [(512, 512), (1003, 1024), (130, 8192), (2000, 4)])
+@pytest.mark.parametrize("nr,nc", [(512, 512), (1003, 1024), (130, 8192), (2000, 4), (301, 6000), (77, 2048)])
 def test_dense_one_pass_matches_two_passes_and_oracle(nr, nc):
     """One pass over B per iteration (rows staged by bulk asynchronous copies)
     against the two-pass kernels and the FP64 oracle; ragged row blocks and
