@@ -1329,6 +1329,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         if (SMEM_RING) F = min(F, (s.R - maxoff - 2) / kTileW);
         if (SMEM_TICKS) F = min(F, (s.RW - maxoff - 1) / kTileW);
         F = min(F, max(1, p.tiles_per_phase));
+        if (p.mode == MODE_HALO) F = min(F, 1);      // one tile per phase: the halo pass walks two tiles
         if (F < 1) {
             if (threadIdx.x == 0) set_error(p.err, kErrUnsupported, day);
             continue;
@@ -1366,12 +1367,18 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 }
                 __syncthreads();
             }
-            for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
+            // halo pass: only the phases that reach the first rows or midnight
+            auto reaches = [&](int pb) {
+                const int sp = min(F, (p.N - pb + kTileW - 1) / kTileW) * kTileW;
+                return pb < p.halo_rows || pb + sp + maxoff + 2 > p.N;
+            };
+            int adv = F * kTileW;
+            for (int pb0 = 0; pb0 < p.N; pb0 += adv) {
+                adv = F * kTileW;
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
                 const int ntask = phase_tasks(nt, nbg, p.n_groups);
                 const int span = nt * kTileW;
-                // halo pass: only the phases that reach the first rows or midnight
-                const bool walk = !halo_pass || pb0 < p.halo_rows || pb0 + span + maxoff + 2 > p.N;
+                const bool walk = !halo_pass || reaches(pb0);
                 s.pb = pb0;
                 if (walk && SMEM_TICKS && !tab) {
                     stage_ticks(p, s, tick16_day, tick16_next);
@@ -1451,6 +1458,21 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 }
                 if (threadIdx.x == 0) s_task = 0;
                 __syncthreads();
+                if (halo_pass) {
+                    // jump over the phases it does not need; what the last walked
+                    // phase left for them is not needed either: clear the ring
+                    int nb = pb0 + adv;
+                    while (nb < p.N && !reaches(nb)) nb += adv;
+                    if (SMEM_RING && nb > pb0 + adv) {
+                        const bool carry = s_carry != 0;
+                        for (int i = threadIdx.x; i < p.O * s.R; i += nthr) {
+                            s.lo[i] = 0u;
+                            if (carry) s.hi[i] = 0;
+                        }
+                        __syncthreads();
+                    }
+                    adv = nb - pb0;
+                }
             }
             if (SMEM_RING) {
                 // the last phase's spill rows lie past the end of the day: clear them
