@@ -123,6 +123,21 @@ def test_coupled_corridor_3yr_consecutive_days():
     assert rel_norm(q, qo, axis=(1, 2)).max() < 1e-4
 
 
+def test_coupled_uneven_days():
+    # each day observes its own subset of links: a day's late trips also count
+    # on links that only the next day observes
+    w = synth.corridor_uneven(n_days=4)
+    days = [0, 1, 2, 3]
+    net, sp, counts, mask = inputs(w, days)
+    seen = mask.any(axis=1)                                   # [day][obs] link observed at all
+    assert (seen[1:] & ~seen[:-1]).any()
+    ctx = _ctx(w, sp, counts, mask)
+    q, loss = ctx.solve(30, 5.0)
+    qo, _, lo = net.solve_coupled(sp, counts, mask, iters=30, eta=5.0)
+    np.testing.assert_allclose(loss, lo, rtol=1e-5)
+    assert rel_norm(q, qo, axis=(1, 2)).max() < 1e-4
+
+
 def test_coupled_days_with_fifo_repairs_and_long_trips():
     # 12 one-minute intervals, a 4-link route that takes several intervals:
     # late departures finish on the next day; day 1 slows down sharply so that
