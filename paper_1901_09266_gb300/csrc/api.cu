@@ -40,6 +40,9 @@ struct dode_ctx {
     int4 *d_groute = nullptr;
     std::vector<int2> rtab;                            // [L] (link, (observed column + 1) | event word << 24)
     int2 *d_rtab = nullptr;
+    std::vector<uint32_t> rtab32;                      // [L] the same in 32 bits (link | column + 1 << 11 | event
+                                                       // << 22), when links and columns fit 11 bits; else empty
+    uint32_t *d_rtab32 = nullptr;
     int32_t *d_gptr = nullptr, *d_task_grp = nullptr, *d_rev = nullptr;
     int32_t *d_god_ptr = nullptr, *d_god = nullptr, *d_godr_ptr = nullptr, *d_godr = nullptr, *d_step_ods = nullptr;
     float *d_pt = nullptr;                             // route choice table [D][P][Np]
@@ -257,6 +260,7 @@ int output_plain(dode_ctx *ctx, const void *src, void *dst, size_t bytes, int pt
 struct FusedShape {
     int block, grid, ring_rows, tick_rows, tiles_per_phase;
     int rtab_off;          // byte offset of the route-position table in shared memory, -1 = read from global
+    int rtab_packed;       // the shared copy is the 32-bit table
     size_t smem;
 };
 
@@ -305,12 +309,19 @@ int fused_shape(dode_ctx *ctx, int precision, FusedShape *s) {
     }
     if (F == 0) F = ntiles;
     size_t smem = fused_smem_bytes(ctx, R, RW);
-    // the packed route-position table goes to shared memory when it fits beside the windows
-    const size_t rtab_bytes = align16((size_t)ctx->L * sizeof(int2));
+    // the route-position table goes to shared memory in its 32-bit form when it
+    // fits beside the windows.  The 8-byte form stays in global memory: the
+    // shared memory it would take costs more L1 (which holds the walks' local
+    // stacks) than its loads save.
     s->rtab_off = -1;
-    if (align16(smem) + rtab_bytes <= budget) {
-        s->rtab_off = (int)align16(smem);
-        smem = align16(smem) + rtab_bytes;
+    s->rtab_packed = 0;
+    if (!ctx->rtab32.empty()) {
+        const size_t rtab_bytes = align16((size_t)ctx->L * sizeof(uint32_t));
+        if (align16(smem) + rtab_bytes <= budget) {
+            s->rtab_off = (int)align16(smem);
+            s->rtab_packed = 1;
+            smem = align16(smem) + rtab_bytes;
+        }
     }
     if (smem > budget + reserve)
         return fail(ctx, DODE_ERR_UNSUPPORTED, "route tables of this network do not fit in shared memory");
@@ -379,6 +390,7 @@ void slot_params(const dode_ctx *ctx, const FusedShape &s, FusedParams *p) {
     p->tick_rows = s.tick_rows;
     p->tiles_per_phase = s.tiles_per_phase;
     p->rtab_off = s.rtab_off;
+    p->rtab_packed = s.rtab_packed;
     p->gp = ctx->d_gp;
     p->lab = ctx->d_lab;
     p->rc_bins = ctx->d_rc_bins;
@@ -482,6 +494,13 @@ void build_groups(dode_ctx *ctx, const int32_t *link_tail) {
     ctx->rtab.resize(ctx->L);
     for (int l = 0; l < ctx->L; ++l)
         ctx->rtab[l] = make_int2(ctx->rlinks[l], (ctx->obs_col[ctx->rlinks[l]] + 1) | (ctx->rev[l] << 24));
+    ctx->rtab32.clear();
+    if (ctx->A <= 2048 && ctx->O + 1 <= 2047) {
+        ctx->rtab32.resize(ctx->L);
+        for (int l = 0; l < ctx->L; ++l)
+            ctx->rtab32[l] = (uint32_t)ctx->rlinks[l] | ((uint32_t)(ctx->obs_col[ctx->rlinks[l]] + 1) << 11) |
+                             ((uint32_t)ctx->rev[l] << 22);
+    }
     ctx->god_ptr.assign(1, 0);
     ctx->godr_ptr.assign(1, 0);
     for (int g = 0; g < ctx->G; ++g) {
@@ -523,7 +542,9 @@ FusedParams base_params(dode_ctx *ctx) {
     p.rpack = ctx->d_rpack;
     p.groute = ctx->d_groute;
     p.rtab = ctx->d_rtab;
+    p.rtab32 = ctx->d_rtab32;
     p.rtab_off = -1;
+    p.rtab_packed = 0;
     p.rptr_total = ctx->L;
     p.gptr = ctx->d_gptr;
     p.task_grp = ctx->d_task_grp;
@@ -982,6 +1003,7 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
     CUB(upload(&ctx->d_rpack, ctx->rpack, ctx->stream));
     CUB(upload(&ctx->d_groute, ctx->groute, ctx->stream));
     CUB(upload(&ctx->d_rtab, ctx->rtab, ctx->stream));
+    if (!ctx->rtab32.empty()) CUB(upload(&ctx->d_rtab32, ctx->rtab32, ctx->stream));
     CUB(upload(&ctx->d_gptr, ctx->gptr, ctx->stream));
     CUB(upload(&ctx->d_task_grp, ctx->task_grp, ctx->stream));
     CUB(upload(&ctx->d_rev, ctx->rev, ctx->stream));
@@ -1022,6 +1044,7 @@ void dode_destroy(dode_ctx *ctx) {
     dfree(ctx->d_rpack);
     dfree(ctx->d_groute);
     dfree(ctx->d_rtab);
+    dfree(ctx->d_rtab32);
     dfree(ctx->d_gptr);
     dfree(ctx->d_task_grp);
     dfree(ctx->d_rev);
@@ -1859,6 +1882,7 @@ extern "C" int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float the
     p.tick_rows = sh.tick_rows;
     p.tiles_per_phase = sh.tiles_per_phase;
     p.rtab_off = sh.rtab_off;
+    p.rtab_packed = sh.rtab_packed;
     p.queue = reinterpret_cast<int *>(base);
     CUL(launch_fused(p, prec, grid, sh.block, sh.smem, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));

@@ -71,7 +71,9 @@ struct FusedParams {
     const int2 *rpack;         // [L] (link, observed column or -1) of every route position
     const int4 *groute;        // [P] walk order: (route, first position, links, start depth | own << 8 | OD << 9)
     const int2 *rtab;          // [L] (link, (observed column + 1) | event word << 24) of every route position
-    int rtab_off;              // byte offset of its shared-memory copy, -1 = read it from global memory
+    const uint32_t *rtab32;    // [L] the same as link | (column + 1) << 11 | event word << 22, or null
+    int rtab_off;              // byte offset of a shared-memory copy, -1 = read rtab from global memory
+    int rtab_packed;           // the shared copy is rtab32
     const int32_t *gptr;       // [G+1] routes of each walk group in groute
     const int32_t *task_grp;   // [G] group processing order (largest walk first)
     const int32_t *rev;        // [L] (E << 1) | save of every route position (see build_groups)

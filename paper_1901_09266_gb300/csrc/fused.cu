@@ -95,6 +95,7 @@ struct Shared {
     const int *gptr;      // [G+1] routes of each walk group
     const int *task_grp;  // [G] processing order
     const int2 *rtab;     // [L] route-position table in shared memory, or null
+    const uint32_t *rtab32;  // [L] its 32-bit form in shared memory, or null
     int *carry;           // set once any deposit of this CTA carried into a high word
     int R, RW, pb;
 };
@@ -115,8 +116,18 @@ __device__ __forceinline__ RouteRegs load_route(const FusedParams &p, const Shar
     for (int half = 0; half < 2; ++half) {
         const int j = lane + 32 * half;
         if (j < beta && (half == 0 || beta > 32)) {
-            const int2 x = s.rtab ? s.rtab[l0 + j] : __ldg(&p.rtab[l0 + j]);
-            const int a = x.x, o = (x.y & 0xffffff) - 1, ev = x.y >> 24;
+            int a, o, ev;
+            if (s.rtab32) {
+                const uint32_t w = s.rtab32[l0 + j];
+                a = (int)(w & 0x7ffu);
+                o = (int)((w >> 11) & 0x7ffu) - 1;
+                ev = (int)(w >> 22);
+            } else {
+                const int2 x = s.rtab ? s.rtab[l0 + j] : __ldg(&p.rtab[l0 + j]);
+                a = x.x;
+                o = (x.y & 0xffffff) - 1;
+                ev = x.y >> 24;
+            }
             const int tb = SMEM_TICKS ? a * s.RW - s.pb : a * p.Np;
             int ob = kInactive;
             if (o >= 0 && ((s.colact[o >> 5] >> (o & 31)) & 1u)) ob = SMEM_RING ? o * s.R - s.pb : o * p.Np;
@@ -1261,7 +1272,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     s.groute = groute;
     s.gptr = gptr;
     s.task_grp = task_grp;
-    s.rtab = p.rtab_off >= 0 ? reinterpret_cast<const int2 *>(smem_raw + p.rtab_off) : nullptr;
+    s.rtab = (p.rtab_off >= 0 && !p.rtab_packed) ? reinterpret_cast<const int2 *>(smem_raw + p.rtab_off) : nullptr;
+    s.rtab32 = (p.rtab_off >= 0 && p.rtab_packed) ? reinterpret_cast<const uint32_t *>(smem_raw + p.rtab_off) : nullptr;
     s.hi = SMEM_RING ? reinterpret_cast<int *>(p.gring) + (size_t)blockIdx.x * p.O * s.R : nullptr;
     __shared__ int s_day;
     __shared__ int s_task;
@@ -1282,7 +1294,10 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     for (int i = threadIdx.x; i < p.P; i += nthr) groute[i] = __ldg(&p.groute[i]);
     for (int i = threadIdx.x; i <= p.n_groups; i += nthr) gptr[i] = __ldg(&p.gptr[i]);
     for (int i = threadIdx.x; i < p.n_groups; i += nthr) task_grp[i] = __ldg(&p.task_grp[i]);
-    if (p.rtab_off >= 0) {
+    if (p.rtab_off >= 0 && p.rtab_packed) {
+        uint32_t *rt = reinterpret_cast<uint32_t *>(smem_raw + p.rtab_off);
+        for (int i = threadIdx.x; i < p.rptr_total; i += nthr) rt[i] = __ldg(&p.rtab32[i]);
+    } else if (p.rtab_off >= 0) {
         int2 *rt = reinterpret_cast<int2 *>(smem_raw + p.rtab_off);
         for (int i = threadIdx.x; i < p.rptr_total; i += nthr) rt[i] = __ldg(&p.rtab[i]);
     }
