@@ -938,7 +938,8 @@ __device__ __forceinline__ uint32_t next_day_residual(const FusedParams &p, int 
 // Residual rows [pb, pb + R) of every observed link, as float bits in the
 // accumulator array (rows past the end of the day are zero, or the next day's
 // residuals for a coupled day): 16-byte loads (8 BF16 or 4 FP32 residuals) at
-// aligned row positions, four per thread in flight.
+// aligned row positions, four per thread in flight.  The slot was written by
+// this kernel, so the loads take the L2-coherent path, not the read-only one.
 template <int PREC>
 __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, const void *rb, int day,
                                                bool exact) {
@@ -955,7 +956,7 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
             v[u] = make_uint4(0u, 0u, 0u, 0u);
             if (i < total) {
                 const int o = i / nch, c = c0 + E * (i - o * nch);
-                v[u] = __ldg(reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(rb) +
+                v[u] = __ldcg(reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(rb) +
                                                             ((size_t)o * p.Np + c) * (PREC == 1 ? 2 : 4)));
             }
         }
@@ -1085,7 +1086,7 @@ __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &
         const float4 cv = __ldg(reinterpret_cast<const float4 *>(cnt + cell));
         const uint32_t mw = (__ldg(&mk[(size_t)o * p.Nw + (c >> 5)]) >> (c & 31)) & 0xfu;
         int4 lv = make_int4(0, 0, 0, 0);
-        if (sel >= 0) lv = __ldg(reinterpret_cast<const int4 *>(lab + cell));
+        if (sel >= 0) lv = __ldcg(reinterpret_cast<const int4 *>(lab + cell));
         const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
         const int ll[4] = {lv.x, lv.y, lv.z, lv.w};
         float r4[4];
