@@ -210,9 +210,19 @@ def test_bf16_form_reports_error_and_matches_fp32_loss(c1):
     qo, _, lo = net.solve_days(sp, counts, mask, iters=iters, eta=5.0, n_threads=7)
     err_loss = np.abs(l16 - lo) / lo
     err_q = rel_norm(q16, qo, axis=(1, 2))
-    print(f"BF16 form vs FP64 oracle: loss rel err max {err_loss.max():.3e}, q rel err max {err_q.max():.3e}")
+    # link counts: the BF16 forward map at the oracle's own q, and the fitted counts
+    x16 = _ctx(w, sp, counts, mask, precision=dode.PREC_BF16).forward(qo.astype(np.float32))
+    xo = net.forward_days(sp, qo, n_threads=7)
+    err_x = rel_norm(x16, xo, axis=(1, 2))
+    err_fit = rel_norm(net.forward_days(sp, q16.astype(np.float64), n_threads=7), xo, axis=(1, 2))
+    e32_loss = np.abs(l32 - lo) / lo
+    e32_q = rel_norm(q32, qo, axis=(1, 2))
+    print(f"BF16 form vs FP64 oracle (max over days): loss {err_loss.max():.3e}, q {err_q.max():.3e}, "
+          f"link counts B q {err_x.max():.3e}, fitted counts {err_fit.max():.3e}; "
+          f"FP32 form: loss {e32_loss.max():.3e}, q {e32_q.max():.3e}")
     assert np.all(np.abs(l16 - l32) / l32 < 1e-3)
     assert err_q.max() < 2e-2
+    assert err_x.max() < 1e-2
 
 
 def test_zero_mask_day_keeps_zero_demand(c1):
