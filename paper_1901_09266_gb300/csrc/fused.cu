@@ -270,10 +270,10 @@ __device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s,
 // ring rows that are never flushed and are cleared after the sweep.  LONG:
 // the route has more than 32 links (positions 32.. sit in the second register
 // set).
-template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG, class ST>
+template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB, bool LONG>
 __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
-                                               int T, bool vw, const ST *S, int t, int E, int *stk) {
+                                               int T, bool vw, const long long *S, int t, int E, int *stk) {
     const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     uint32_t Wu = (uint32_t)(S[E + 1] - S[t]);
@@ -369,12 +369,10 @@ __device__ __forceinline__ int walk_start(const FusedParams &p, const int32_t *t
     return stk[s0];
 }
 
-// Route flows of one tile: exclusive prefix sums S over the group's walk order
-// (ST = uint32_t keeps the low words only: enough when the caller walks the
-// integer form, which needs fast).
-template <int PREC, class ST>
+// Route flows of one tile: exclusive prefix sums S over the group's walk order.
+template <int PREC>
 __device__ __forceinline__ void group_flows(const FusedParams &p, const Shared &s, int day, int i0, int m, int b,
-                                            bool vw, ST *S, bool &any, bool &fast) {
+                                            bool vw, long long *S, bool &any, bool &fast) {
     const int bi = min(b, p.N - 1);
     long long acc = 0;
     bool nonneg = true;
@@ -399,7 +397,7 @@ __device__ __forceinline__ void group_flows(const FusedParams &p, const Shared &
                 nonneg = nonneg && fu >= 0;
                 any = any || fu != 0;
                 acc += fu;
-                S[t0 + u + 1] = (ST)acc;
+                S[t0 + u + 1] = acc;
             }
         }
     }
@@ -419,7 +417,7 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
     // exclusive prefix sums over the group's walk order
     long long S[kGroupRoutes + 1];
     bool any, fast_lane;
-    group_flows<PREC, long long>(p, s, day, i0, m, b, vw, S, any, fast_lane);
+    group_flows<PREC>(p, s, day, i0, m, b, vw, S, any, fast_lane);
     if (!__any_sync(0xffffffffu, any)) return;            // nothing departs: no deposits
     const bool fast = __all_sync(0xffffffffu, fast_lane);
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
@@ -447,16 +445,19 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
 
 // Two tiles of the same walk group in one warp (A: boundaries b0 .., B: b0 + 31 ..):
 // the route record shuffles and loop control are shared, the two lane chains
-// are independent.  Integer form, routes of at most 32 links.
+// are independent.  Integer form, routes of at most 32 links.  The prefix sums
+// and the walk stack hold both chains' values side by side (one 8-byte local
+// access for the pair).
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                                 const int32_t *trowA, const int32_t *trowB, const RouteRegs &rr,
                                                 float *gacc, int j0, int beta, int TA, int TB, bool vwA, bool vwB,
-                                                const uint32_t *SA, const uint32_t *SB, int t, int E, int *stkA,
-                                                int *stkB) {
+                                                const uint2 *S2, int t, int E, int2 *stk2) {
     const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
-    uint32_t WuA = SA[E + 1] - SA[t], WuB = SB[E + 1] - SB[t];
+    uint2 shi = S2[E + 1];
+    const uint2 slo = S2[t];
+    uint32_t WuA = shi.x - slo.x, WuB = shi.y - slo.y;
     float WfA = __uint2float_rn(WuA), WfB = __uint2float_rn(WuB);
     for (int j = j0; j < beta; ++j) {
         const int tb = __shfl_sync(0xffffffffu, rr.t0, j & 31);
@@ -464,8 +465,9 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
         const int ev = __shfl_sync(0xffffffffu, rr.e0, j & 31);
         if ((ev >> 1) != E) {
             E = ev >> 1;
-            WuA = SA[E + 1] - SA[t];
-            WuB = SB[E + 1] - SB[t];
+            shi = S2[E + 1];
+            WuA = shi.x - slo.x;
+            WuB = shi.y - slo.y;
             WfA = __uint2float_rn(WuA);
             WfB = __uint2float_rn(WuB);
         }
@@ -519,14 +521,58 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
         }
         TA = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowA, j, TA, tb, h0A);
         TB = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowB, j, TB, tb, h0B);
-        if (ev & 1) {
-            stkA[j + 1] = TA;
-            stkB[j + 1] = TB;
-        }
+        if (ev & 1) stk2[j + 1] = make_int2(TA, TB);
     }
 }
 
+// Route flows of both tiles of a pair task: exclusive prefix sums interleaved
+// per route (x: tile A, y: tile B), so that one 8-byte local access serves both
+// chains; 32 bits suffice for the integer form the pair walk takes (fast).
+template <int PREC>
+__device__ __forceinline__ void group_flows2(const FusedParams &p, const Shared &s, int day, int i0, int m, int bA,
+                                             int bB, bool vwA, bool vwB, uint2 *S, bool &any, bool &fast) {
+    const int biA = min(bA, p.N - 1), biB = min(bB, p.N - 1);
+    long long accA = 0, accB = 0;
+    bool nonneg = true;
+    any = false;
+    S[0] = make_uint2(0u, 0u);
+    for (int t0 = 0; t0 < m; t0 += 4) {
+        float pa[4], qa[4], pb[4], qb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            pa[u] = qa[u] = pb[u] = qb[u] = 0.f;
+            if (t0 + u < m) {
+                const int4 gr = s.groute[i0 + t0 + u];
+                const size_t prow = ((size_t)day * p.P + gr.x) * p.Np, qrow = ((size_t)day * p.K + (gr.w >> 9)) * p.Np;
+                if (vwA) {
+                    pa[u] = __ldg(&p.pt[prow + biA]);
+                    qa[u] = Operand<PREC>::q(p, qrow + bA);
+                }
+                if (vwB) {
+                    pb[u] = __ldg(&p.pt[prow + biB]);
+                    qb[u] = Operand<PREC>::q(p, qrow + bB);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (t0 + u < m) {
+                const long long fa = __float2ll_rn(pa[u] * qa[u] * kFxScale);
+                const long long fb = __float2ll_rn(pb[u] * qb[u] * kFxScale);
+                nonneg = nonneg && fa >= 0 && fb >= 0;
+                any = any || fa != 0 || fb != 0;
+                accA += fa;
+                accB += fb;
+                S[t0 + u + 1] = make_uint2((uint32_t)accA, (uint32_t)accB);
+            }
+        }
+    }
+    fast = nonneg && accA < (1ll << 31) && accB < (1ll << 31);
+}
+
 // Forward task over both tiles of a phase for walk group g (b0 .. b0 + 61).
+// Groups with a route past 32 links, or with a flow outside the integer form,
+// take two single-tile tasks.
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, int g, int b0, const int32_t *tab) {
     const int lane = threadIdx.x & 31;
@@ -535,18 +581,19 @@ __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, in
     const bool vwA = (lane < kTileW) && (bA < p.N), vwB = (lane < kTileW) && (bB < p.N);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
-    uint32_t SA[kGroupRoutes + 1], SB[kGroupRoutes + 1];   // the pair walk is integer-form only
-    bool anyA, anyB, fastA, fastB;
-    group_flows<PREC, uint32_t>(p, s, day, i0, m, bA, vwA, SA, anyA, fastA);
-    group_flows<PREC, uint32_t>(p, s, day, i0, m, bB, vwB, SB, anyB, fastB);
-    if (!__any_sync(0xffffffffu, anyA || anyB)) return;
-    if (!__all_sync(0xffffffffu, fastA && fastB)) {
+    uint2 S2[kGroupRoutes + 1];   // the pair walk is integer-form only
+    bool any, fast;
+    group_flows2<PREC>(p, s, day, i0, m, bA, bB, vwA, vwB, S2, any, fast);
+    if (!__any_sync(0xffffffffu, any)) return;
+    bool longr = false;                                   // a route past 32 links: single-tile walks
+    for (int t = 0; t < m; ++t) longr = longr || s.groute[i0 + t].z > 32;
+    if (longr || !__all_sync(0xffffffffu, fast)) {
         forward_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0, tab);
         forward_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0 + kTileW, tab);
         return;
     }
     float *gacc = SMEM_RING ? nullptr : p.gring + (size_t)blockIdx.x * p.O * p.Np;
-    int stkA[kMaxRouteLinks + 1], stkB[kMaxRouteLinks + 1];
+    int2 stk2[kMaxRouteLinks + 1];
     for (int t = 0; t < m; ++t) {
         const int4 gr = s.groute[i0 + t];
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
@@ -554,18 +601,21 @@ __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, in
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trowA = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bbA : nullptr;
         const int32_t *trowB = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bbB : nullptr;
-        const int TA = walk_start<TAB>(p, trowA, stkA, s0, bbA);
-        const int TB = walk_start<TAB>(p, trowB, stkB, s0, bbB);
-        const int E = __shfl_sync(0xffffffffu, s0 < 32 ? rr.e0 : rr.e1, s0 & 31) >> 1;
-        if (beta <= 32) {
-            forward_walk_u2<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trowA, trowB, rr, gacc, s0, beta, TA, TB,
-                                                             vwA, vwB, SA, SB, t, E, stkA, stkB);
+        int TA, TB;
+        if (s0 == 0) {
+            TA = p.div.ipt * bbA;
+            TB = p.div.ipt * bbB;
+        } else if (TAB) {
+            TA = __ldg(&trowA[(size_t)s0 * (p.N + 1)]);
+            TB = __ldg(&trowB[(size_t)s0 * (p.N + 1)]);
         } else {
-            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowA, rr, gacc, s0, beta, TA, vwA,
-                                                                   SA, t, E, stkA);
-            forward_walk_u<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowB, rr, gacc, s0, beta, TB, vwB,
-                                                                   SB, t, E, stkB);
+            const int2 st = stk2[s0];
+            TA = st.x;
+            TB = st.y;
         }
+        const int E = __shfl_sync(0xffffffffu, rr.e0, s0 & 31) >> 1;
+        forward_walk_u2<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trowA, trowB, rr, gacc, s0, beta, TA, TB, vwA,
+                                                         vwB, S2, t, E, stk2);
     }
 }
 
@@ -708,7 +758,7 @@ template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                               const int32_t *trowA, const int32_t *trowB, const RouteRegs &rr,
                                               const void *rb, int j0, int beta, int TA, int TB, float &GA, float &GB,
-                                              bool vwA, bool vwB, int *stkA, int *stkB, float *gstkA, float *gstkB) {
+                                              bool vwA, bool vwB, int2 *stk2, float2 *gstk2) {
     const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
     const float *racc = SMEM_RING ? reinterpret_cast<const float *>(s.lo) : nullptr;
     for (int j = j0; j < beta; ++j) {
@@ -754,15 +804,15 @@ __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared
         TA = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowA, j, TA, tb, h0A);
         TB = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowB, j, TB, tb, h0B);
         if (ev & 1) {
-            stkA[j + 1] = TA;
-            gstkA[j + 1] = GA;
-            stkB[j + 1] = TB;
-            gstkB[j + 1] = GB;
+            stk2[j + 1] = make_int2(TA, TB);
+            gstk2[j + 1] = make_float2(GA, GB);
         }
     }
 }
 
-// Adjoint task over both tiles of a phase for walk group g (b0 .. b0 + 61).
+// Adjoint task over both tiles of a phase for walk group g (b0 .. b0 + 61);
+// stacks and route sums hold both tiles' values side by side.  Groups with a
+// route past 32 links take two single-tile tasks.
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS, bool TAB>
 __device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, int g, int b0, const void *rb,
                               const int32_t *tab, double *s_dth) {
@@ -773,31 +823,44 @@ __device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, in
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int N = p.N;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    bool longr = false;                                   // a route past 32 links: single-tile walks
+    for (int t = 0; t < m; ++t) longr = longr || s.groute[i0 + t].z > 32;
+    if (longr) {
+        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0, rb, tab, s_dth);
+        adjoint_task<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, day, g, b0 + kTileW, rb, tab, s_dth);
+        return;
+    }
     float *gp = p.gp + (size_t)blockIdx.x * p.P * p.Np;
-    int stkA[kMaxRouteLinks + 1], stkB[kMaxRouteLinks + 1];
-    float gstkA[kMaxRouteLinks + 1], gstkB[kMaxRouteLinks + 1];
-    float gplA[kGroupRoutes], gplB[kGroupRoutes];
+    int2 stk2[kMaxRouteLinks + 1];
+    float2 gstk2[kMaxRouteLinks + 1];
+    float2 gpl2[kGroupRoutes];
     for (int t = 0; t < m; ++t) {
         const int4 gr = s.groute[i0 + t];
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trowA = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bbA : nullptr;
         const int32_t *trowB = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bbB : nullptr;
-        const int TA = walk_start<TAB>(p, trowA, stkA, s0, bbA);
-        const int TB = walk_start<TAB>(p, trowB, stkB, s0, bbB);
-        float GA = s0 == 0 ? 0.f : gstkA[s0];
-        float GB = s0 == 0 ? 0.f : gstkB[s0];
-        if (beta <= 32) {
-            adjoint_walk2<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trowA, trowB, rr, rb, s0, beta, TA, TB, GA,
-                                                           GB, vwA, vwB, stkA, stkB, gstkA, gstkB);
+        int TA, TB;
+        float GA = 0.f, GB = 0.f;
+        if (s0 == 0) {
+            TA = p.div.ipt * bbA;
+            TB = p.div.ipt * bbB;
         } else {
-            GA = adjoint_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowA, rr, rb, s0, beta, TA, GA,
-                                                                      vwA, stkA, gstkA);
-            GB = adjoint_walk<PREC, SMEM_RING, SMEM_TICKS, TAB, true>(p, s, tick_day, trowB, rr, rb, s0, beta, TB, GB,
-                                                                      vwB, stkB, gstkB);
+            if (TAB) {
+                TA = __ldg(&trowA[(size_t)s0 * (N + 1)]);
+                TB = __ldg(&trowB[(size_t)s0 * (N + 1)]);
+            } else {
+                const int2 st = stk2[s0];
+                TA = st.x;
+                TB = st.y;
+            }
+            const float2 gs = gstk2[s0];
+            GA = gs.x;
+            GB = gs.y;
         }
-        gplA[t] = GA;
-        gplB[t] = GB;
+        adjoint_walk2<PREC, SMEM_RING, SMEM_TICKS, TAB>(p, s, tick_day, trowA, trowB, rr, rb, s0, beta, TA, TB, GA, GB,
+                                                       vwA, vwB, stk2, gstk2);
+        gpl2[t] = make_float2(GA, GB);
         if (!((gr.w >> 8) & 1)) {
             if (vwA) gp[(size_t)k * p.Np + bA] = GA;
             if (vwB) gp[(size_t)k * p.Np + bB] = GB;
@@ -812,10 +875,10 @@ __device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, in
         const int od = __ldg(&p.god[e]), nr = __ldg(&p.godr_ptr[e + 1]) - r0;
         if (vwA)
             od_update<PREC>(p, day, od, bA, nr, [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
-                            [&](int i) { return gplA[__ldg(&gr[i])]; }, dth);
+                            [&](int i) { return gpl2[__ldg(&gr[i])].x; }, dth);
         if (vwB)
             od_update<PREC>(p, day, od, bB, nr, [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
-                            [&](int i) { return gplB[__ldg(&gr[i])]; }, dth);
+                            [&](int i) { return gpl2[__ldg(&gr[i])].y; }, dth);
     }
     if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
 }

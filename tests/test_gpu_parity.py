@@ -319,6 +319,39 @@ def test_device_pointers_roundtrip(c1):
     assert rel_norm(qd.cpu().numpy(), qh) < 1e-6
 
 
+def test_route_longer_than_32_links():
+    # a 45-link route (positions 32.. sit in the walk's second register set;
+    # pair tasks fall back to single-tile walks) with congestion on a few links
+    L, N = 45, 64
+    lengths = [0.3 + 0.05 * (i % 7) for i in range(L)]
+    sp = np.full((2, N, L), 55.0, np.float32)
+    sp[0, 20:30, 5:9] = 22.0
+    sp[1, 40:50, 33:40] = 18.0
+    w, sp = single_path_workload(lengths, sp, interval_s=120, obs=list(range(0, L, 2)))
+    net = orc.Net.from_workload(w)
+    assert net.day(sp[0]).n_repairs == 0 and net.day(sp[1]).n_repairs == 0
+    qt = np.random.default_rng(9).gamma(2.0, 5.0, (2, N, 1))
+    counts = (net.forward_days(sp, qt) * 1.03).astype(np.float32)
+    for prec in (dode.PREC_FP32, dode.PREC_BF16):
+        ctx = dode.Context.from_workload(w, precision=prec)
+        ctx.set_days(counts, sp)
+        if prec == dode.PREC_FP32:
+            x = ctx.forward(qt.astype(np.float32))
+            for d in range(2):
+                xo = net.day(sp[d]).forward(qt[d])
+                np.testing.assert_allclose(x[d], xo, rtol=0, atol=1e-5 * np.abs(xo).max())
+        q, loss = ctx.solve(100, 5.0)
+        qo, _, lo = net.solve_days(sp, counts, np.ones_like(counts, np.uint8), iters=100, eta=5.0)
+        if prec == dode.PREC_FP32:
+            loss_close(loss, lo, counts, None)
+            assert rel_norm(q, qo, axis=(1, 2)).max() < 1e-4
+        else:
+            # the target is fitted almost exactly, so the BF16 form's floor is its
+            # own resolution: BF16 demands put ~2^-8 relative error on every count
+            floor = 2.0 ** -16 * (counts.astype(np.float64) ** 2).sum(axis=(1, 2))
+            assert np.all(np.abs(loss - lo) <= 2e-3 * lo + floor), (loss, lo, floor)
+
+
 def test_long_link_reads_ticks_from_global():
     # a 20-mile link at 15 mph takes 80 minutes = 76800 ticks: more than 16 bits,
     # so the tick window is not staged in shared memory
