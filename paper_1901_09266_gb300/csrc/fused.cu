@@ -1459,7 +1459,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 const int span = nt * kTileW;
                 const bool walk = !halo_pass || reaches(pb0);
                 s.pb = pb0;
-                if (walk && SMEM_TICKS && !tab) {
+                // the solve and evaluation passes stage each later phase's ticks during the previous flush
+                if (walk && SMEM_TICKS && !tab && (halo_pass || pb0 == 0)) {
                     stage_ticks(p, s, tick16_day, tick16_next);
                     __syncthreads();
                 }
@@ -1508,6 +1509,12 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                                                        ks, kc);
                 else
                     flush_solve<PREC, SMEM_RING>(p, s, gacc, rb, cnt, mk, lab, sel, pb0, rows, carry, ks, kc);
+                if (SMEM_TICKS && !tab && !halo_pass && pb0 + adv < p.N) {
+                    // the tasks are done with the tick window: stage the next phase's rows now
+                    s.pb = pb0 + adv;
+                    stage_ticks(p, s, tick16_day, tick16_next);
+                    s.pb = pb0;
+                }
                 if (SMEM_RING) {
                     // move the spill rows [span, span + spill) to the front, zero the rest
                     __syncthreads();
