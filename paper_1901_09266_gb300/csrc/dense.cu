@@ -8,7 +8,7 @@
 //   k_dense_grad   g = B^T r        a CTA per (block of rows, 1024 columns),
 //                                   each thread a 4-column strip, 16-byte
 //                                   loads; partial gradients per row block
-//   k_dense_step   sums the partials in CTA order, then G += g^2,
+//   k_dense_step   sums the partials in a fixed order, then G += g^2,
 //                  x = max(x - eta g / (sqrt(G) + eps), 0)
 // All sums have a fixed order: results do not depend on timing.
 #include "dode_internal.cuh"
@@ -140,13 +140,23 @@ __global__ void __launch_bounds__(256) k_dense_grad(const float *__restrict__ B,
                 if (j < m) gp[(size_t)(c + u) * m + j] = acc[u][j];
 }
 
-// g = sum of the partials in CTA order; Adagrad step and projection.
+// g = sum of the partials in a fixed order; Adagrad step and projection.  A
+// CTA takes 32 entries; warp w sums the partials b = w, w + 8, ... of each
+// (coalesced rows of 32), and the eight warp sums are added in warp order.
 __global__ void __launch_bounds__(256) k_dense_step(const float *__restrict__ gpart, int n_part, int nc, int m,
                                                     float eta, float eps, float *__restrict__ x, float *__restrict__ G) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nc * m) return;
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t ne = (size_t)nc * m;
+    const size_t e = (size_t)blockIdx.x * 32 + lane;
     float g = 0.f;
-    for (int b = 0; b < n_part; ++b) g += gpart[(size_t)b * nc * m + e];
+    if (e < ne)
+        for (int b = warp; b < n_part; b += 8) g += gpart[(size_t)b * ne + e];
+    red[warp][lane] = g;
+    __syncthreads();
+    if (warp != 0 || e >= ne) return;
+    g = 0.f;
+    for (int w = 0; w < 8; ++w) g += red[w][lane];
     const float Gv = G[e] + g * g;
     G[e] = Gv;
     x[e] = fmaxf(x[e] - eta * g / (sqrtf(Gv) + eps), 0.f);
@@ -305,7 +315,7 @@ cudaError_t dense_fused_iteration(const DenseParams &p, int grid, int RB, size_t
     k_dense_fused<<<grid, 256, smem, s>>>(p, RB, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_dense_step<<<(p.nc + 255) / 256, 256, 0, s>>>(p.gpart, grid, p.nc, 1, p.eta, p.eps, p.x, p.G);
+    k_dense_step<<<(p.nc + 31) / 32, 256, 0, s>>>(p.gpart, grid, p.nc, 1, p.eta, p.eps, p.x, p.G);
     return cudaGetLastError();
 }
 
@@ -322,7 +332,7 @@ cudaError_t dense_iteration(const DenseParams &p, bool step, cudaStream_t s) {
     k_dense_grad<<<gg, 256, (size_t)p.rows_per_cta * p.m * sizeof(float), s>>>(p.B, p.r, p.nr, p.nc, p.m, p.vec,
                                                                                 p.rows_per_cta, p.gpart);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_dense_step<<<(p.nc * p.m + 255) / 256, 256, 0, s>>>(p.gpart, p.grid_g, p.nc, p.m, p.eta, p.eps, p.x, p.G);
+    k_dense_step<<<(p.nc * p.m + 31) / 32, 256, 0, s>>>(p.gpart, p.grid_g, p.nc, p.m, p.eta, p.eps, p.x, p.G);
     return cudaGetLastError();
 }
 
