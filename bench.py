@@ -327,15 +327,19 @@ def run_gpu(args):
         ctx.solve(E, args.step, args.batch, q_out=q_n, loss_out=l_n)
 
     e2e_value = None
+    e2e_clk = None
     if args.e2e_steps > 0:
         step_host()
         torch.cuda.synchronize()
         dist_barrier()
+        clocks_e2e = ClockSampler(local)
+        clocks_e2e.start()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             step_host()
         torch.cuda.synchronize()
         e2e_s = dist_max(time.perf_counter() - t0)
+        e2e_clk = clocks_e2e.stop()
         e2e_value = D * E * args.e2e_steps * world / e2e_s
     h2d = sp.nbytes + counts.nbytes + mask.nbytes
     d2h = q_n.nbytes + l_n.nbytes
@@ -510,7 +514,7 @@ def run_gpu(args):
                        "launch": tuned or {"block": args.block, "ctas_per_sm": args.ctas},
                        "l2": "inputs larger than L2 (reloaded every step)"},
             "e2e": {"value": e2e_value, "unit": "day-iter/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h), "clocks": e2e_clk},
             "gpu_launches": int(launches),
             "roofline": roof,
             "issue_roofline": issue,
