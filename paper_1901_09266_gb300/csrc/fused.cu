@@ -1401,6 +1401,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         // coupled days: every day keeps the context's largest offset, so that the
         // rows carried between phases always cover the halo rows
         const int maxoff = p.coupled ? p.halo_rows - 2 : p.maxoff[day];
+        int tw_pb = -1;                   // phase whose tick rows the window holds (this day)
         // tiles per phase: the accumulators must hold a phase's arrival rows
         // (31 F + maxoff + 2) and the tick window its trajectories' entry rows
         // (31 F + maxoff + 1)
@@ -1460,8 +1461,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 const bool walk = !halo_pass || reaches(pb0);
                 s.pb = pb0;
                 // the solve and evaluation passes stage each later phase's ticks during the previous flush
-                if (walk && SMEM_TICKS && !tab && (halo_pass || pb0 == 0)) {
+                if (walk && SMEM_TICKS && !tab && (halo_pass || pb0 == 0) && tw_pb != pb0) {
                     stage_ticks(p, s, tick16_day, tick16_next);
+                    tw_pb = pb0;
                     __syncthreads();
                 }
                 while (walk) {
@@ -1513,6 +1515,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     // the tasks are done with the tick window: stage the next phase's rows now
                     s.pb = pb0 + adv;
                     stage_ticks(p, s, tick16_day, tick16_next);
+                    tw_pb = pb0 + adv;
                     s.pb = pb0;
                 }
                 if (SMEM_RING) {
@@ -1583,12 +1586,19 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             }
 
             // ------------------------------ adjoint sweep ------------------------------
-            for (int pb0 = 0; pb0 < p.N; pb0 += F * kTileW) {
+            // last phase first: it still holds the forward's last tick window, and
+            // the next forward sweep starts from the window this sweep ends with
+            const int nph = (p.N + F * kTileW - 1) / (F * kTileW);
+            for (int ph = nph - 1; ph >= 0; --ph) {
+                const int pb0 = ph * F * kTileW;
                 const int nt = min(F, (p.N - pb0 + kTileW - 1) / kTileW);
                 const int ntask = phase_tasks(nt, nbg, p.n_groups);
                 s.pb = pb0;
                 __syncthreads();                           // previous phase done with the windows
-                if (SMEM_TICKS && !tab) stage_ticks(p, s, tick16_day, tick16_next);
+                if (SMEM_TICKS && !tab && tw_pb != pb0) {
+                    stage_ticks(p, s, tick16_day, tick16_next);
+                    tw_pb = pb0;
+                }
                 if (SMEM_RING) stage_residual<PREC>(p, s, rb, day, exact);
                 __syncthreads();
                 while (true) {
