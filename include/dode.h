@@ -119,10 +119,10 @@ typedef struct {
                                 day d + 1's link times and counts on day d + 1's links (its first
                                 maxoff + 2 intervals); the gradient of day d's demand then includes
                                 day d + 1's residuals.  The last loaded day drops mass after its
-                                midnight as the per-day problem does.  Needs the fused form,
-                                row_chunk = 0 and a network whose accumulator ring and tick window
-                                fit in shared memory (else DODE_ERR_UNSUPPORTED at the first
-                                evaluation).  Each epoch then takes two launches; use_graph is
+                                midnight as the per-day problem does.  Needs the fused form and
+                                row_chunk = 0 (else dode_create returns DODE_ERR_ARG), and a
+                                network whose accumulator ring and tick window fit in shared
+                                memory (else DODE_ERR_UNSUPPORTED at the first evaluation).  Each epoch then takes two launches; use_graph is
                                 ignored.  dode_dar_distance, dode_get_dar and
                                 dode_loss_static_scratch refuse coupled days.  0 = independent
                                 days (default). */
