@@ -203,13 +203,20 @@ def gpu_inputs(w, days):
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
 
+_ORACLE_INPUTS: dict = {}
+
+
 def oracle_rate(w, days, epochs: int, threads: int):
+    """The FP64 oracle's day-iterations per second on these days (inputs built
+    once per process and not timed)."""
     from oracle import oracle as orc
-    net = orc.Net.from_workload(w)
-    sp = w.speeds(days)
-    x = net.forward_days(sp, w.q_true(days).astype(np.float64), n_threads=threads)
-    counts = w.counts_from(x, days)
-    mask = w.mask(days)
+    key = (w.name, w.n_days, tuple(days))
+    if key not in _ORACLE_INPUTS:
+        net = orc.Net.from_workload(w)
+        sp = w.speeds(days)
+        x = net.forward_days(sp, w.q_true(days).astype(np.float64), n_threads=threads)
+        _ORACLE_INPUTS[key] = (net, sp, w.counts_from(x, days), w.mask(days))
+    net, sp, counts, mask = _ORACLE_INPUTS[key]
     t0 = time.perf_counter()
     net.solve_days(sp, counts, mask, iters=epochs, eta=5.0, n_threads=threads, day_ids=np.asarray(days))
     dt = time.perf_counter() - t0
@@ -559,7 +566,7 @@ def main(argv=None):
     ap.add_argument("--dense-n", type=int, default=6000)
     ap.add_argument("--dense-iters", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--ref-days", type=int, default=128)
+    ap.add_argument("--ref-days", type=int, default=1096)
     ap.add_argument("--ref-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
