@@ -678,28 +678,15 @@ __device__ __forceinline__ float adjoint_walk(const FusedParams &p, const Shared
         const int hi = __shfl_down_sync(0xffffffffu, T, 1);
         const int h0 = interval_of(T, p.div);
         if (ob != kInactive) {
-            if (SMEM_RING) {
-                // one- and two-cell windows without a branch (a one-cell window has
-                // d0 = 1); the rare longer window takes the tail loop
+            if (SMEM_RING || (vw && h0 < N)) {
                 const int idx = ob + h0;
                 const int e0 = h0 * ipt + ipt;
                 const float inv = __fdividef(1.f, (float)(hi - T));
                 const float d0 = first_share<PREC>(T, e0, inv);
-                const float r0 = racc[idx];
-                float a = fmaf(1.f - d0, racc[idx + 1], d0 * r0);
-                if (hi > e0 + ipt)
-                    a = d0 * r0 + window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt,
-                                                                       inv, d0, 0.f);
-                G += a;
-            } else if (vw && h0 < N) {
-                const int idx = ob + h0;
-                const int e0 = h0 * ipt + ipt;
-                const float inv = __fdividef(1.f, (float)(hi - T));
-                const float d0 = first_share<PREC>(T, e0, inv);
-                float a = d0 * Operand<PREC>::r(rb, (size_t)idx);
-                if (hi > e0 && h0 + 1 < N) {
+                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                if (hi > e0 && (SMEM_RING || h0 + 1 < N)) {
                     if (hi <= e0 + ipt)
-                        a += (1.f - d0) * Operand<PREC>::r(rb, (size_t)idx + 1);
+                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
                     else
                         a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt, inv,
                                                                  d0, 0.f);
@@ -783,56 +770,30 @@ __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared
         const int h0A = interval_of(TA, p.div);
         const int h0B = interval_of(TB, p.div);
         if (ob != kInactive) {
-            if (SMEM_RING) {
-                // one- and two-cell windows without a branch (a one-cell window has
-                // d0 = 1); the rare longer window takes the tail loop
+            if (SMEM_RING || (vwA && h0A < N)) {
                 const int idx = ob + h0A;
                 const int e0 = h0A * ipt + ipt;
                 const float inv = __fdividef(1.f, (float)(hiA - TA));
                 const float d0 = first_share<PREC>(TA, e0, inv);
-                const float r0 = racc[idx];
-                float a = fmaf(1.f - d0, racc[idx + 1], d0 * r0);
-                if (hiA > e0 + ipt)
-                    a = d0 * r0 + window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiA, e0, h0A + 1, N, ipt,
-                                                                       inv, d0, 0.f);
-                GA += a;
-            } else if (vwA && h0A < N) {
-                const int idx = ob + h0A;
-                const int e0 = h0A * ipt + ipt;
-                const float inv = __fdividef(1.f, (float)(hiA - TA));
-                const float d0 = first_share<PREC>(TA, e0, inv);
-                float a = d0 * Operand<PREC>::r(rb, (size_t)idx);
-                if (hiA > e0 && h0A + 1 < N) {
+                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                if (hiA > e0 && (SMEM_RING || h0A + 1 < N)) {
                     if (hiA <= e0 + ipt)
-                        a += (1.f - d0) * Operand<PREC>::r(rb, (size_t)idx + 1);
+                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
                     else
                         a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiA, e0, h0A + 1, N, ipt, inv,
                                                                  d0, 0.f);
                 }
                 GA += a;
             }
-            if (SMEM_RING) {
-                // one- and two-cell windows without a branch (a one-cell window has
-                // d0 = 1); the rare longer window takes the tail loop
+            if (SMEM_RING || (vwB && h0B < N)) {
                 const int idx = ob + h0B;
                 const int e0 = h0B * ipt + ipt;
                 const float inv = __fdividef(1.f, (float)(hiB - TB));
                 const float d0 = first_share<PREC>(TB, e0, inv);
-                const float r0 = racc[idx];
-                float a = fmaf(1.f - d0, racc[idx + 1], d0 * r0);
-                if (hiB > e0 + ipt)
-                    a = d0 * r0 + window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiB, e0, h0B + 1, N, ipt,
-                                                                       inv, d0, 0.f);
-                GB += a;
-            } else if (vwB && h0B < N) {
-                const int idx = ob + h0B;
-                const int e0 = h0B * ipt + ipt;
-                const float inv = __fdividef(1.f, (float)(hiB - TB));
-                const float d0 = first_share<PREC>(TB, e0, inv);
-                float a = d0 * Operand<PREC>::r(rb, (size_t)idx);
-                if (hiB > e0 && h0B + 1 < N) {
+                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                if (hiB > e0 && (SMEM_RING || h0B + 1 < N)) {
                     if (hiB <= e0 + ipt)
-                        a += (1.f - d0) * Operand<PREC>::r(rb, (size_t)idx + 1);
+                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
                     else
                         a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiB, e0, h0B + 1, N, ipt, inv,
                                                                  d0, 0.f);
