@@ -15,14 +15,19 @@ SRC = os.path.join(HERE, "dode_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one oracle source file into the shared library ``out``."""
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", src, "-o", out + ".tmp", "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
 def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
-    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", SRC, "-o", LIB + ".tmp", "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(LIB + ".tmp", LIB)
-    return LIB
+    return compile_source(SRC, LIB)
 
 
 if __name__ == "__main__":

@@ -27,65 +27,69 @@ _u8p = ct.POINTER(ct.c_uint8)
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ct.CDLL(path)
-        L.or_net_create.restype = ct.c_void_p
-        L.or_net_create.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _f32p, ct.c_int32,
-                                    ct.c_int32, _i32p, _i32p, _i32p, ct.c_int32, _i32p]
-        L.or_net_destroy.argtypes = [ct.c_void_p]
-        L.or_day_build.restype = ct.c_void_p
-        L.or_day_build.argtypes = [ct.c_void_p, _f32p, ct.c_double, ct.POINTER(ct.c_int)]
-        L.or_day_destroy.argtypes = [ct.c_void_p]
-        L.or_day_set_theta.argtypes = [ct.c_void_p, ct.c_double]
-        L.or_day_n_dar.restype = ct.c_int64
-        L.or_day_n_dar.argtypes = [ct.c_void_p]
-        L.or_day_nnz.restype = ct.c_int64
-        L.or_day_nnz.argtypes = [ct.c_void_p]
-        L.or_day_repairs.restype = ct.c_int64
-        L.or_day_repairs.argtypes = [ct.c_void_p]
-        L.or_day_get_ticks.argtypes = [ct.c_void_p, _i32p]
-        L.or_day_get_traj.argtypes = [ct.c_void_p, _i64p]
-        L.or_day_get_dar.argtypes = [ct.c_void_p, _i32p, _f64p]
-        L.or_day_get_route_choice.argtypes = [ct.c_void_p, _f64p, _f64p]
-        L.or_day_get_B.argtypes = [ct.c_void_p, _i32p, _i32p, _f64p]
-        L.or_day_dense_B.argtypes = [ct.c_void_p, _f64p]
-        L.or_forward.argtypes = [ct.c_void_p, _f64p, _f64p]
-        L.or_adjoint.argtypes = [ct.c_void_p, _f64p, _f64p]
-        L.or_residual.restype = ct.c_double
-        L.or_residual.argtypes = [ct.c_void_p, _f64p, _f32p, _u8p, _f64p]
-        L.or_solve_day.restype = ct.c_double
-        L.or_solve_day.argtypes = [ct.c_void_p, _f32p, _u8p, ct.c_int32, ct.c_double, ct.c_double,
-                                   ct.c_int32, ct.c_uint64, ct.c_int32, _f64p, _f64p, _f64p]
-        L.or_loss_grad_day.restype = ct.c_double
-        L.or_loss_grad_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p, _f64p, _f64p, _f64p]
-        L.or_r2_day.restype = ct.c_double
-        L.or_r2_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p]
-        L.or_splitmix64_next.restype = ct.c_uint64
-        L.or_splitmix64_next.argtypes = [ct.POINTER(ct.c_uint64)]
-        L.or_splitmix64_at.restype = ct.c_uint64
-        L.or_splitmix64_at.argtypes = [ct.c_uint64, ct.c_uint64]
-        L.or_permute_rows.argtypes = [_i32p, ct.c_int32, ct.c_uint64, ct.c_int32, ct.c_int32]
-        L.or_solve_days.restype = ct.c_int
-        L.or_solve_days.argtypes = [ct.c_void_p, ct.c_int32, _i32p, _f32p, _f32p, _u8p, ct.c_double, _f64p,
-                                    ct.c_int32, ct.c_double, ct.c_double, ct.c_int32, ct.c_uint64,
-                                    ct.c_int32, _f64p, _f64p, _f64p]
-        L.or_day_set_choice_times.argtypes = [ct.c_void_p, _f64p]
-        L.or_forward_days.restype = ct.c_int
-        L.or_forward_days.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, ct.c_int32,
-                                      _f64p]
-        L.or_forward_coupled.restype = ct.c_int
-        L.or_forward_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, _f64p]
-        L.or_solve_coupled.restype = ct.c_int
-        L.or_solve_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, ct.c_int32,
-                                       ct.c_double, ct.c_double, _f64p, _f64p, _f64p, _f64p]
-        L.or_loss_grad_coupled.restype = ct.c_int
-        L.or_loss_grad_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, _f64p,
-                                           _f64p, _f64p, _f64p, _f64p]
-        L.or_coupled_day_dar.restype = ct.c_int
-        L.or_coupled_day_dar.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _f32p, _i32p, _i64p, _i32p,
-                                         _f64p]
-        _lib = L
+        _lib = bind(_build.build())
     return _lib
+
+
+def bind(path: str):
+    """Load an oracle library and declare its entry points."""
+    L = ct.CDLL(path)
+    L.or_net_create.restype = ct.c_void_p
+    L.or_net_create.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int32, _f32p, ct.c_int32,
+                                ct.c_int32, _i32p, _i32p, _i32p, ct.c_int32, _i32p]
+    L.or_net_destroy.argtypes = [ct.c_void_p]
+    L.or_day_build.restype = ct.c_void_p
+    L.or_day_build.argtypes = [ct.c_void_p, _f32p, ct.c_double, ct.POINTER(ct.c_int)]
+    L.or_day_destroy.argtypes = [ct.c_void_p]
+    L.or_day_set_theta.argtypes = [ct.c_void_p, ct.c_double]
+    L.or_day_n_dar.restype = ct.c_int64
+    L.or_day_n_dar.argtypes = [ct.c_void_p]
+    L.or_day_nnz.restype = ct.c_int64
+    L.or_day_nnz.argtypes = [ct.c_void_p]
+    L.or_day_repairs.restype = ct.c_int64
+    L.or_day_repairs.argtypes = [ct.c_void_p]
+    L.or_day_get_ticks.argtypes = [ct.c_void_p, _i32p]
+    L.or_day_get_traj.argtypes = [ct.c_void_p, _i64p]
+    L.or_day_get_dar.argtypes = [ct.c_void_p, _i32p, _f64p]
+    L.or_day_get_route_choice.argtypes = [ct.c_void_p, _f64p, _f64p]
+    L.or_day_get_B.argtypes = [ct.c_void_p, _i32p, _i32p, _f64p]
+    L.or_day_dense_B.argtypes = [ct.c_void_p, _f64p]
+    L.or_forward.argtypes = [ct.c_void_p, _f64p, _f64p]
+    L.or_adjoint.argtypes = [ct.c_void_p, _f64p, _f64p]
+    L.or_residual.restype = ct.c_double
+    L.or_residual.argtypes = [ct.c_void_p, _f64p, _f32p, _u8p, _f64p]
+    L.or_solve_day.restype = ct.c_double
+    L.or_solve_day.argtypes = [ct.c_void_p, _f32p, _u8p, ct.c_int32, ct.c_double, ct.c_double,
+                               ct.c_int32, ct.c_uint64, ct.c_int32, _f64p, _f64p, _f64p]
+    L.or_loss_grad_day.restype = ct.c_double
+    L.or_loss_grad_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p, _f64p, _f64p, _f64p]
+    L.or_r2_day.restype = ct.c_double
+    L.or_r2_day.argtypes = [ct.c_void_p, _f32p, _u8p, _f64p]
+    L.or_splitmix64_next.restype = ct.c_uint64
+    L.or_splitmix64_next.argtypes = [ct.POINTER(ct.c_uint64)]
+    L.or_splitmix64_at.restype = ct.c_uint64
+    L.or_splitmix64_at.argtypes = [ct.c_uint64, ct.c_uint64]
+    L.or_permute_rows.argtypes = [_i32p, ct.c_int32, ct.c_uint64, ct.c_int32, ct.c_int32]
+    L.or_solve_days.restype = ct.c_int
+    L.or_solve_days.argtypes = [ct.c_void_p, ct.c_int32, _i32p, _f32p, _f32p, _u8p, ct.c_double, _f64p,
+                                ct.c_int32, ct.c_double, ct.c_double, ct.c_int32, ct.c_uint64,
+                                ct.c_int32, _f64p, _f64p, _f64p]
+    L.or_day_set_choice_times.argtypes = [ct.c_void_p, _f64p]
+    L.or_forward_days.restype = ct.c_int
+    L.or_forward_days.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, ct.c_int32,
+                                  _f64p]
+    L.or_forward_coupled.restype = ct.c_int
+    L.or_forward_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f64p, ct.c_double, _f64p]
+    L.or_solve_coupled.restype = ct.c_int
+    L.or_solve_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, ct.c_int32,
+                                   ct.c_double, ct.c_double, _f64p, _f64p, _f64p, _f64p]
+    L.or_loss_grad_coupled.restype = ct.c_int
+    L.or_loss_grad_coupled.argtypes = [ct.c_void_p, ct.c_int32, _f32p, _f32p, _u8p, ct.c_double, _f64p,
+                                       _f64p, _f64p, _f64p, _f64p]
+    L.or_coupled_day_dar.restype = ct.c_int
+    L.or_coupled_day_dar.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, _f32p, _i32p, _i64p, _i32p,
+                                     _f64p]
+    return L
 
 
 def _p(a: np.ndarray, t):
@@ -105,7 +109,7 @@ class Net:
 
     def __init__(self, n_intervals: int, interval_s: int, ticks_per_s: int, link_len_mi, route_ptr,
                  route_links, route_od, n_od: int, obs_links):
-        L = lib()
+        self._L = L = lib()          # the library that owns this handle
         self.N, self.interval_s, self.tps = int(n_intervals), int(interval_s), int(ticks_per_s)
         self.ipt = self.interval_s * self.tps
         self._len = _c(link_len_mi, np.float32)
@@ -126,8 +130,8 @@ class Net:
                    w.routes.route_links, w.routes.route_od, w.routes.n_od, w.net.obs_links)
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.or_net_destroy(self.h)
+        if getattr(self, "h", None) and getattr(self, "_L", None) is not None:
+            self._L.or_net_destroy(self.h)
             self.h = None
 
     def day(self, speeds: np.ndarray, theta: float = 0.1) -> "Day":
@@ -145,7 +149,7 @@ class Net:
         loss = np.zeros(D)
         ids = None if day_ids is None else _c(day_ids, np.int32)
         cc = None if choice_times is None else _c(choice_times, np.float64)
-        rc = lib().or_solve_days(self.h, D, None if ids is None else _p(ids, _i32p), _p(sp, _f32p),
+        rc = self._L.or_solve_days(self.h, D, None if ids is None else _p(ids, _i32p), _p(sp, _f32p),
                                  _p(ct_, _f32p), _p(mk, _u8p), theta, None if cc is None else _p(cc, _f64p),
                                  iters, eta, eps, row_chunk,
                                  ct.c_uint64(seed), n_threads, _p(q, _f64p), _p(G, _f64p), _p(loss, _f64p))
@@ -157,7 +161,7 @@ class Net:
         D = speeds.shape[0]
         sp, qq = _c(speeds, np.float32), _c(q, np.float64)
         x = np.zeros((D, self.N, self.O))
-        rc = lib().or_forward_days(self.h, D, _p(sp, _f32p), _p(qq, _f64p), theta, n_threads, _p(x, _f64p))
+        rc = self._L.or_forward_days(self.h, D, _p(sp, _f32p), _p(qq, _f64p), theta, n_threads, _p(x, _f64p))
         if rc != 0:
             raise OracleError(f"or_forward_days rc={rc}")
         return x
@@ -168,7 +172,7 @@ class Net:
         D = speeds.shape[0]
         sp, qq = _c(speeds, np.float32), _c(q, np.float64)
         x = np.zeros((D, self.N, self.O))
-        rc = lib().or_forward_coupled(self.h, D, _p(sp, _f32p), _p(qq, _f64p), theta, _p(x, _f64p))
+        rc = self._L.or_forward_coupled(self.h, D, _p(sp, _f32p), _p(qq, _f64p), theta, _p(x, _f64p))
         if rc != 0:
             raise OracleError(f"or_forward_coupled rc={rc}")
         return x
@@ -183,7 +187,7 @@ class Net:
         G = np.zeros((D, self.N, self.K)) if G0 is None else _c(G0, np.float64).copy()
         loss = np.zeros(D)
         tr = np.zeros((max(iters, 1), D))
-        rc = lib().or_solve_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta, iters, eta,
+        rc = self._L.or_solve_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta, iters, eta,
                                     eps, _p(q, _f64p), _p(G, _f64p), _p(loss, _f64p),
                                     _p(tr, _f64p) if trace else None)
         if rc != 0:
@@ -197,7 +201,7 @@ class Net:
         sp, ct_, mk, qq = _c(speeds, np.float32), _c(counts, np.float32), _c(mask, np.uint8), _c(q, np.float64)
         loss, dth, dabs = np.zeros(D), np.zeros(D), np.zeros(D)
         dq = np.zeros((D, self.N, self.K))
-        rc = lib().or_loss_grad_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta,
+        rc = self._L.or_loss_grad_coupled(self.h, D, _p(sp, _f32p), _p(ct_, _f32p), _p(mk, _u8p), theta,
                                         _p(qq, _f64p), _p(loss, _f64p), _p(dq, _f64p), _p(dth, _f64p),
                                         _p(dabs, _f64p))
         if rc != 0:
@@ -210,12 +214,12 @@ class Net:
         D = speeds.shape[0]
         sp = _c(speeds, np.float32)
         Nh, n = ct.c_int32(0), ct.c_int64(0)
-        rc = lib().or_coupled_day_dar(self.h, D, i, _p(sp, _f32p), ct.byref(Nh), ct.byref(n), None, None)
+        rc = self._L.or_coupled_day_dar(self.h, D, i, _p(sp, _f32p), ct.byref(Nh), ct.byref(n), None, None)
         if rc != 0:
             raise OracleError(f"or_coupled_day_dar rc={rc}")
         kjh = np.zeros((n.value, 4), np.int32)
         rho = np.zeros(n.value)
-        lib().or_coupled_day_dar(self.h, D, i, _p(sp, _f32p), ct.byref(Nh), ct.byref(n), _p(kjh, _i32p),
+        self._L.or_coupled_day_dar(self.h, D, i, _p(sp, _f32p), ct.byref(Nh), ct.byref(n), _p(kjh, _i32p),
                                  _p(rho, _f64p))
         return Nh.value, kjh, rho
 
@@ -228,33 +232,34 @@ class Day:
         self._sp = _c(speeds, np.float32)
         assert self._sp.shape == (net.N, net.A)
         err = ct.c_int(0)
-        self.h = lib().or_day_build(net.h, _p(self._sp, _f32p), theta, ct.byref(err))
+        self._L = net._L
+        self.h = self._L.or_day_build(net.h, _p(self._sp, _f32p), theta, ct.byref(err))
         if not self.h:
             raise OracleError(f"or_day_build rc={err.value}")
 
     def __del__(self):
-        if getattr(self, "h", None) and _lib is not None:
-            _lib.or_day_destroy(self.h)
+        if getattr(self, "h", None) and getattr(self, "_L", None) is not None:
+            self._L.or_day_destroy(self.h)
             self.h = None
 
     def set_theta(self, theta: float) -> None:
-        lib().or_day_set_theta(self.h, theta)
+        self._L.or_day_set_theta(self.h, theta)
 
     def set_choice_times(self, Cc) -> None:
         """Route choice from travel times Cc [N][P] (minutes), None = own."""
         if Cc is None:
-            lib().or_day_set_choice_times(self.h, None)
+            self._L.or_day_set_choice_times(self.h, None)
         else:
             cc = _c(Cc, np.float64)
-            lib().or_day_set_choice_times(self.h, _p(cc, _f64p))
+            self._L.or_day_set_choice_times(self.h, _p(cc, _f64p))
 
     @property
     def n_repairs(self) -> int:
-        return int(lib().or_day_repairs(self.h))
+        return int(self._L.or_day_repairs(self.h))
 
     def ticks(self) -> np.ndarray:
         out = np.zeros((self.net.N, self.net.A), np.int32)
-        lib().or_day_get_ticks(self.h, _p(out, _i32p))
+        self._L.or_day_get_ticks(self.h, _p(out, _i32p))
         return out
 
     def trajectories(self) -> list:
@@ -262,7 +267,7 @@ class Day:
         n = self.net
         total = int(n.route_ptr[-1]) + n.P
         out = np.zeros((total, n.N + 1), np.int64)
-        lib().or_day_get_traj(self.h, _p(out, _i64p))
+        self._L.or_day_get_traj(self.h, _p(out, _i64p))
         res = []
         for k in range(n.P):
             s = int(n.route_ptr[k]) + k
@@ -272,10 +277,10 @@ class Day:
 
     def dar(self):
         """(kjh [n][4] = (k, j, h1, h2), rho [n]) in emission order."""
-        m = int(lib().or_day_n_dar(self.h))
+        m = int(self._L.or_day_n_dar(self.h))
         kjh = np.zeros((m, 4), np.int32)
         rho = np.zeros(m)
-        lib().or_day_get_dar(self.h, _p(kjh, _i32p), _p(rho, _f64p))
+        self._L.or_day_get_dar(self.h, _p(kjh, _i32p), _p(rho, _f64p))
         return kjh, rho
 
     def route_choice(self):
@@ -283,40 +288,40 @@ class Day:
         n = self.net
         C = np.zeros((n.N, n.P))
         p = np.zeros((n.N, n.P))
-        lib().or_day_get_route_choice(self.h, _p(C, _f64p), _p(p, _f64p))
+        self._L.or_day_get_route_choice(self.h, _p(C, _f64p), _p(p, _f64p))
         return C, p
 
     def B_coo(self):
-        m = int(lib().or_day_nnz(self.h))
+        m = int(self._L.or_day_nnz(self.h))
         r, c, v = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m)
-        lib().or_day_get_B(self.h, _p(r, _i32p), _p(c, _i32p), _p(v, _f64p))
+        self._L.or_day_get_B(self.h, _p(r, _i32p), _p(c, _i32p), _p(v, _f64p))
         return r, c, v
 
     def dense_B(self) -> np.ndarray:
         n = self.net
         Bd = np.zeros((n.N * n.O, n.N * n.K))
-        lib().or_day_dense_B(self.h, _p(Bd, _f64p))
+        self._L.or_day_dense_B(self.h, _p(Bd, _f64p))
         return Bd
 
     def forward(self, q: np.ndarray) -> np.ndarray:
         n = self.net
         qq = _c(q, np.float64).reshape(n.N, n.K)
         x = np.zeros((n.N, n.O))
-        lib().or_forward(self.h, _p(qq, _f64p), _p(x, _f64p))
+        self._L.or_forward(self.h, _p(qq, _f64p), _p(x, _f64p))
         return x
 
     def adjoint(self, r: np.ndarray) -> np.ndarray:
         n = self.net
         rr = _c(r, np.float64).reshape(n.N, n.O)
         g = np.zeros((n.N, n.K))
-        lib().or_adjoint(self.h, _p(rr, _f64p), _p(g, _f64p))
+        self._L.or_adjoint(self.h, _p(rr, _f64p), _p(g, _f64p))
         return g
 
     def residual(self, xhat, counts, mask):
         n = self.net
         xx, cc, mm = _c(xhat, np.float64), _c(counts, np.float32), _c(mask, np.uint8)
         r = np.zeros((n.N, n.O))
-        loss = lib().or_residual(self.h, _p(xx, _f64p), _p(cc, _f32p), _p(mm, _u8p), _p(r, _f64p))
+        loss = self._L.or_residual(self.h, _p(xx, _f64p), _p(cc, _f32p), _p(mm, _u8p), _p(r, _f64p))
         return loss, r
 
     def solve(self, counts, mask, iters=200, eta=5.0, eps=1e-10, row_chunk=0, seed=0, day=0,
@@ -326,7 +331,7 @@ class Day:
         q = np.zeros((n.N, n.K)) if q0 is None else _c(q0, np.float64).copy()
         G = np.zeros((n.N, n.K)) if G0 is None else _c(G0, np.float64).copy()
         tr = np.zeros(max(iters, 1)) if trace else None
-        loss = lib().or_solve_day(self.h, _p(cc, _f32p), _p(mm, _u8p), iters, eta, eps, row_chunk,
+        loss = self._L.or_solve_day(self.h, _p(cc, _f32p), _p(mm, _u8p), iters, eta, eps, row_chunk,
                                   ct.c_uint64(seed), day, _p(q, _f64p), _p(G, _f64p),
                                   None if tr is None else _p(tr, _f64p))
         return (q, G, loss, tr[:iters]) if trace else (q, G, loss)
@@ -334,7 +339,7 @@ class Day:
     def r2(self, counts, mask, q) -> float:
         """R^2 of the link counts implied by q against the observed counts."""
         cc, mm, qq = _c(counts, np.float32), _c(mask, np.uint8), _c(q, np.float64)
-        return float(lib().or_r2_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p)))
+        return float(self._L.or_r2_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p)))
 
     def loss_grad(self, counts, mask, q, with_scale=False):
         """(loss, dL/dq, dL/dtheta) -- and, with ``with_scale``, the sum of the
@@ -344,7 +349,7 @@ class Day:
         dq = np.zeros((n.N, n.K))
         dth = ct.c_double(0.0)
         dabs = ct.c_double(0.0)
-        loss = lib().or_loss_grad_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p), _p(dq, _f64p),
+        loss = self._L.or_loss_grad_day(self.h, _p(cc, _f32p), _p(mm, _u8p), _p(qq, _f64p), _p(dq, _f64p),
                                       ct.byref(dth), ct.byref(dabs))
         return (loss, dq, dth.value, dabs.value) if with_scale else (loss, dq, dth.value)
 

@@ -43,6 +43,20 @@ def test_coupled_forward_equals_one_long_day():
     assert np.abs(indep[1:, :12] - got[1:, :12]).max() > 1e-3 * np.abs(got).max()
 
 
+def test_coupled_days_run_on_the_next_days_speeds_after_midnight():
+    # the first hour of days 1 and 2 slowed down: the previous evening's late trips
+    # run on those speeds once past midnight, as on one long day
+    w, net, sp, q = _setup()
+    sp = sp.copy()
+    sp[1, :12] *= 0.6
+    sp[2, :12] *= 0.8
+    D, N = sp.shape[0], w.n_intervals
+    day = _long_net(w, D).day(sp.reshape(D * N, -1))
+    assert day.n_repairs == 0
+    want = day.forward(q.reshape(D * N, -1)).reshape(D, N, -1)
+    assert rel_norm(net.forward_coupled(sp, q), want) < 1e-13
+
+
 def test_coupled_solve_equals_one_long_day():
     w, net, sp, _ = _setup()
     D, N = sp.shape[0], w.n_intervals

@@ -82,6 +82,23 @@ def test_trajectories_constant_speed_are_cumulative_sums():
     np.testing.assert_array_equal(p, 1.0)
 
 
+def test_link_time_is_taken_at_link_entry():
+    # Sec. 2.4 (omega_1 = t^2 - (t^1 + c_1(t^1))): a link's travel time is the one of
+    # the interval in which the vehicle enters that link, not the departure interval;
+    # entries after the last interval take the last interval's time.
+    # link 0: 2 mi at 20 mph = 360 s = 5760 ticks in every interval;
+    # link 1: 1 mi at 60 / 30 / 15 mph in intervals 0 / 1 / 2 = 960 / 1920 / 3840 ticks
+    N = 3
+    net = _single_path_net([2.0, 1.0], N)
+    sp = np.array([[20.0, 60.0], [20.0, 30.0], [20.0, 15.0]], np.float32)
+    day = net.day(sp)
+    T = day.trajectories()[0]
+    np.testing.assert_array_equal(T[1], [5760, 10560, 15360, 20160])
+    # link 1 entered in interval 1, 2, 3 (past the table) and 4 (past the table)
+    np.testing.assert_array_equal(T[2], [5760 + 1920, 10560 + 3840, 15360 + 3840, 20160 + 3840])
+    assert day.n_repairs == 0
+
+
 def test_fifo_repair_and_point_mass():
     # link 1 (2 mi) takes 10 mph in interval 0 (11520 ticks) and 64 mph afterwards
     # (1800 ticks): the vehicle of boundary 1 would overtake the one of boundary 0.
@@ -330,6 +347,19 @@ def test_masked_rows_do_not_count():
     assert a[2] == b[2]
 
 
+def test_masked_rows_do_not_count_in_row_chunks():
+    # Algorithm 1 permutes and chunks the observed rows only
+    w, day, q_true, counts = _tiny_instance(noise=0.1)
+    mask = np.ones_like(counts, np.uint8)
+    mask[1, :] = 0
+    garbage = counts.copy()
+    garbage[1, :] = 1e6
+    a = day.solve(counts, mask, iters=50, row_chunk=3, seed=2)
+    b = day.solve(garbage, mask, iters=50, row_chunk=3, seed=2)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[2] == b[2]
+
+
 def test_row_chunk_covering_all_rows_equals_full_batch():
     w, day, q_true, counts = _tiny_instance(noise=0.1)
     mask = np.ones_like(counts, np.uint8)
@@ -502,6 +532,9 @@ def test_pattern_route_choice_pins():
     C1, _ = net.day(sp[1]).route_choice()
     C2, p2 = net.day(sp[2]).route_choice()
     np.testing.assert_array_equal(Cc[2], C2)                 # pattern -1: own times
+    Cs = orc.pattern_choice_times(net, sp, [-1, 3, -1])
+    np.testing.assert_array_equal(Cs[0], C0)                 # several days without a pattern
+    np.testing.assert_array_equal(Cs[2], C2)
     np.testing.assert_allclose(Cc[0], 0.5 * (C0 + C1), rtol=1e-15)
     # a one-day pattern is the day's own route choice
     d = net.day(sp[2])
