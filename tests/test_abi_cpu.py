@@ -96,3 +96,47 @@ def test_interval_magic_division_is_exact():
         t = t.astype(np.uint64)
         got = ((t * np.uint64(magic)) >> np.uint64(32)) >> np.uint64(ll - 1)
         np.testing.assert_array_equal(got, t // np.uint64(ipt))
+
+
+def test_validation_rejects_bad_options(lib):
+    """dode_create checks its options before it touches a device."""
+    w = synth.corridor_7day()
+
+    def expect(code, **opt):
+        with pytest.raises(dode.DodeError) as e:
+            dode.Context.from_workload(w, **opt)
+        assert e.value.code == code, opt
+
+    # consecutive days are solved jointly by the fused form with full-row updates only
+    expect(dode.ERR_ARG, couple_days=1, form=dode.FORM_PLAIN)
+    expect(dode.ERR_ARG, couple_days=1, row_chunk=64)
+    expect(dode.ERR_ARG, couple_days=2)
+    expect(dode.ERR_ARG, form=9)
+    expect(dode.ERR_ARG, precision=7)
+    expect(dode.ERR_ARG, row_chunk=-1)
+    expect(dode.ERR_ARG, theta_per_min=float("nan"))
+    expect(dode.ERR_ARG, eps=-1.0)
+    expect(dode.ERR_ARG, block_threads=-1)
+    expect(dode.ERR_ARG, ctas_per_sm=-1)
+    expect(dode.ERR_ARG, n_intervals=0)
+    # an interval of 2 .. 2^24 ticks and a day of at most 2^29 ticks
+    expect(dode.ERR_ARG, interval_s=1, ticks_per_s=1)
+    expect(dode.ERR_ARG, interval_s=1 << 21, ticks_per_s=16)
+    expect(dode.ERR_ARG, n_intervals=1 << 16, interval_s=1000, ticks_per_s=16)
+
+
+def test_validation_rejects_routes_longer_than_64_links(lib):
+    L = 65
+    tail = np.arange(L, dtype=np.int32)
+    args = dict(n_nodes=L + 1, link_tail=tail, link_head=tail + 1, link_len_mi=np.ones(L, np.float32),
+                obs_links=np.array([0], np.int32), n_od=1, route_od=np.array([0], np.int32),
+                route_ptr=np.array([0, L], np.int32), route_links=tail)
+    with pytest.raises(dode.DodeError) as e:
+        dode.Context(**args)
+    assert e.value.code == dode.ERR_ARG
+    # 64 links pass validation and reach the device (absent on a host without a GPU)
+    args.update(route_ptr=np.array([0, L - 1], np.int32), route_links=tail[:L - 1])
+    try:
+        dode.Context(**args).close()
+    except dode.DodeError as e:
+        assert e.code != dode.ERR_ARG
