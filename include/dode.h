@@ -140,6 +140,13 @@ void dode_default_options(dode_options *opt);
  * Errors: DODE_ERR_ARG (sizes, ids out of range, duplicated observed link, bad
  * option), DODE_ERR_ROUTE_NOT_CONTIGUOUS, DODE_ERR_ROUTE_REPEATS_LINK,
  * DODE_ERR_CUDA / DODE_ERR_OOM.  On error *out is NULL.
+ * Limits checked here, before any device call (DODE_ERR_ARG):
+ *   - every link length finite and > 0; every OD pair has at least one route;
+ *   - a route has 1 .. 64 links; fewer than 2^22 OD pairs;
+ *   - an interval of 2 .. 2^24 ticks (interval_s * ticks_per_s), a day of at
+ *     most 2^29 ticks;
+ *   - row_chunk > 0 needs n_intervals * n_obs < 2^31 (row ids are int32);
+ *   - couple_days = 1 needs the fused form and row_chunk = 0.
  */
 int dode_create(const dode_network *net, const dode_routes *routes, const dode_options *opt,
                 dode_ctx **out);
