@@ -279,6 +279,26 @@ def test_small_day_and_midnight_crossing():
     assert rel_norm(q, qo, axis=(1, 2)).max() < 1e-4
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(form=dode.FORM_PLAIN), dict(precision=dode.PREC_BF16),
+                                dict(couple_days=1)], ids=["fused", "plain", "bf16", "coupled"])
+def test_zero_epochs_return_the_state_and_its_loss(c1, kw):
+    # Algorithm 1 with no epoch: q stays at q0 = 0 and the loss is that of q = 0,
+    # the sum of the observed counts squared; after 20 epochs, zero more return
+    # that state and its loss
+    w, net, sp, counts, mask = c1
+    ctx = _ctx(w, sp, counts, mask, **kw)
+    q, loss = ctx.solve(0, 5.0)
+    assert not q.any()
+    want = (np.where(mask > 0, counts.astype(np.float64), 0.0) ** 2).sum(axis=(1, 2))
+    _, _, lo = net.solve_days(sp, counts, mask, iters=0)
+    np.testing.assert_allclose(lo, want, rtol=1e-12)
+    loss_close(loss, want, counts, mask)
+    q20, l20 = ctx.solve(20, 5.0)
+    q0, l0 = ctx.solve(0, 5.0)
+    np.testing.assert_array_equal(q0, q20)
+    np.testing.assert_allclose(l0, l20, rtol=1e-6)
+
+
 def test_errors_are_reported(c1):
     w, net, sp, counts, mask = c1
     ctx = dode.Context.from_workload(w)
