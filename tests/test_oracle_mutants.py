@@ -74,6 +74,15 @@ MUTANTS = [
     # Sec. 2.4: travel times quantised to ticks
     ("ticks_truncated", "float r = nearbyintf(t);", "float r = truncf(t);", ["ticks_closed_form"]),
     ("ticks_round_half_away", "float r = nearbyintf(t);", "float r = roundf(t);", ["ticks_closed_form"]),
+    ("ticks_in_double_precision",
+     "volatile float num = n->len_mi[a] * scale;  /* fl32(len * 3600 tps) */\n"
+     "            volatile float t = num / v;                  /* fl32(num / v) */\n"
+     "            if (!(t <= 16777216.0f)) return OR_ERR_TICK_OVERFLOW;\n"
+     "            float r = nearbyintf(t);",
+     "volatile double num = (double)n->len_mi[a] * (double)scale;\n"
+     "            volatile double t = num / v;\n"
+     "            if (!(t <= 16777216.0)) return OR_ERR_TICK_OVERFLOW;\n"
+     "            double r = nearbyint(t);", ["ticks_closed_form"]),
     ("ticks_no_floor_of_one", "ticks[(size_t)h * n->A + a] = c < 1 ? 1 : c;",
      "ticks[(size_t)h * n->A + a] = c;", ["ticks_closed_form"]),
     ("speed_not_checked", "if (!(v > 0.0f) || !isfinite(v)) return OR_ERR_BAD_SPEED;", "",

@@ -36,14 +36,18 @@ def _single_path_net(lengths, n_intervals, interval_s=300, tps=16, obs=None):
 
 def test_ticks_closed_form():
     # 1 mi at 60 mph = 60 s = 960 ticks; 1.5 mi at 45 mph = 120 s; 0.25 mi at 35 mph = 25.714 s
-    net = _single_path_net([1.0, 1.5, 0.25, 0.5, 0.875, 1e-6], 1)
-    sp = np.array([[60.0, 45.0, 35.0, 11520.0, 14400.0, 65.0]], np.float32)
+    net = _single_path_net([1.0, 1.5, 0.25, 0.5, 0.875, 1e-6, 0.1], 1)
+    sp = np.array([[60.0, 45.0, 35.0, 11520.0, 14400.0, 65.0, 2304.0]], np.float32)
     t = net.day(sp).ticks()[0]
     assert t[0] == 960 and t[1] == 1920
     assert t[2] == 411                       # 411.43 rounds down
     assert t[3] == 2                         # exactly 2.5 ticks: round half to even
     assert t[4] == 4                         # exactly 3.5 ticks: round half to even
     assert t[5] == 1                         # never below one tick
+    # the quantisation is FP32 arithmetic: 0.1 mi is 0.100000001490116... in FP32, whose
+    # product with 57600 (5760.0000858...) rounds to 5760 in FP32, and 5760 / 2304 = 2.5
+    # exactly, which rounds half to even to 2; in FP64 the quotient 2.50000004 rounds to 3
+    assert t[6] == 2
 
 
 @pytest.mark.parametrize("bad", [0.0, -5.0, np.nan, np.inf])
