@@ -68,11 +68,13 @@ def test_ticks_bit_exact(c1):
 
 
 def test_ticks_rounding_cases():
-    sp = np.array([[60.0, 45.0, 35.0, 11520.0, 14400.0, 65.0]] * 3, np.float32)
-    w, sp = single_path_workload([1.0, 1.5, 0.25, 0.5, 0.875, 1e-6], sp)
+    # the last link: 0.1 mi at 2304 mph is 2.5 ticks in FP32 (round half to even: 2),
+    # 2.50000004 in FP64
+    sp = np.array([[60.0, 45.0, 35.0, 11520.0, 14400.0, 65.0, 2304.0]] * 3, np.float32)
+    w, sp = single_path_workload([1.0, 1.5, 0.25, 0.5, 0.875, 1e-6, 0.1], sp)
     ctx = dode.Context.from_workload(w)
-    ctx.set_days(np.zeros((1, 3, 6), np.float32), sp)
-    np.testing.assert_array_equal(ctx.ticks(0)[0], [960, 1920, 411, 2, 4, 1])
+    ctx.set_days(np.zeros((1, 3, 7), np.float32), sp)
+    np.testing.assert_array_equal(ctx.ticks(0)[0], [960, 1920, 411, 2, 4, 1, 2])
 
 
 def test_route_times_offsets_and_dar(c1):
