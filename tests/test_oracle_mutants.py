@@ -8,10 +8,12 @@ that should catch the mistake run, and at least one of them must fail. The
 unmutated source must pass every pin the C cases name, through the same
 harness, so that a broken harness cannot pass for a caught mistake.
 
-One kind of mistake no pin can see: a constant factor on Algorithm 1's
-gradient (2 B^T r instead of B^T r). Adagrad divides the step by the root of
-the accumulated squared gradients, so the iterates do not change, up to the
-eps in the denominator.
+Two kinds of change no pin can see, because they change no result:
+- a constant factor on Algorithm 1's gradient (2 B^T r instead of B^T r).
+  Adagrad divides the step by the root of the accumulated squared gradients,
+  so the iterates do not change, up to the eps in the denominator;
+- leaving the last coupled day's next-day residual rows unset. That day's
+  horizon ends at its midnight, so its B never reads them.
 
 Mutations are chosen to keep every memory access in bounds, so a mutant fails
 an assertion instead of crashing the test process.
@@ -49,6 +51,7 @@ PINS = {
     "exact_recovery": pp.test_exact_recovery_noise_free,
     "bruteforce_nnls_kkt": pp.test_spgd_reaches_bruteforce_nnls_and_kkt,
     "masked_rows": pp.test_masked_rows_do_not_count,
+    "one_adagrad_step": pp.test_one_adagrad_step_closed_form,
     "masked_rows_in_chunks": pp.test_masked_rows_do_not_count_in_row_chunks,
     "one_chunk_equals_full_batch": pp.test_row_chunk_covering_all_rows_equals_full_batch,
     "row_chunks_converge": pp.test_row_chunks_converge_to_nnls,
@@ -95,12 +98,18 @@ MUTANTS = [
      ["link_time_at_entry"]),
     ("link_time_next_interval", "int64_t h = t / n->ipt;", "int64_t h = t / n->ipt + 1;",
      ["link_time_at_entry", "example_dar", "fifo_repair_and_point_mass"]),
+    ("trajectory_starts_one_interval_late", "T[traj_index(n, k, 0, b)] = (int64_t)n->ipt * b;",
+     "T[traj_index(n, k, 0, b)] = (int64_t)n->ipt * (b + 1);", ["constant_speed_trajectories", "example_dar"]),
     ("no_fifo_repair", "if (nxt < prev) { nxt = prev; ++rep; }", "",
      ["fifo_repair_and_point_mass"]),
     ("fifo_against_previous_link", "int64_t prev = T[traj_index(n, k, j + 1, b - 1)];",
      "int64_t prev = T[traj_index(n, k, j, b - 1)];", ["fifo_repair_and_point_mass", "dar_partitions"]),
     # Eq. (dar)
     ("point_mass_dropped", "if (h2 < Nh) {", "if (0) {", ["fifo_repair_and_point_mass"]),
+    ("point_mass_in_next_interval", "int64_t h2 = lo / ipt;\n                    if (h2 < Nh) {",
+     "int64_t h2 = lo / ipt + 1;\n                    if (h2 < Nh) {", ["fifo_repair_and_point_mass"]),
+    ("first_partial_interval_skipped", "for (int64_t h2 = lo / ipt;", "for (int64_t h2 = (lo + ipt - 1) / ipt;",
+     ["example_link_path", "dar_partitions"]),
     ("rho_over_interval_length", "out[m].rho = (double)(e - s) / (double)(hi - lo);",
      "out[m].rho = (double)(e - s) / (double)ipt;", ["example_dar", "dar_partitions"]),
     ("overlap_ignores_window_end", "int64_t e = hi < ipt * (h2 + 1) ? hi : ipt * (h2 + 1);",
@@ -118,6 +127,12 @@ MUTANTS = [
      "(double)(d->T[traj_index(n, k, beta - 1, h)] - (int64_t)n->ipt * h)",
      ["constant_speed_trajectories"]),
     # Eq. (assign), (reverse): B = rho * p, forward and adjoint
+    ("route_time_from_first_link_exit",
+     "(double)(d->T[traj_index(n, k, beta, h)] - (int64_t)n->ipt * h)",
+     "(double)(d->T[traj_index(n, k, beta, h)] - d->T[traj_index(n, k, 1, h)])",
+     ["constant_speed_trajectories"]),
+    ("B_row_at_departure_interval", "d->b_row[m] = x->h2 * n->O + o;", "d->b_row[m] = x->h1 * n->O + o;",
+     ["two_tap_shift", "coupled_forward_long_day"]),
     ("B_without_route_share", "d->b_val[m] = x->rho * d->p[(size_t)x->h1 * n->P + x->k];",
      "d->b_val[m] = x->rho;", ["conservation_and_transpose"]),
     ("B_share_of_arrival_interval", "d->b_val[m] = x->rho * d->p[(size_t)x->h1 * n->P + x->k];",
@@ -132,6 +147,10 @@ MUTANTS = [
      "r[i] = xhat[i] - (double)counts[i];", ["masked_rows", "r2"]),
     ("adagrad_without_root", "q[i] -= eta * g[i] / (sqrt(G[i]) + eps);",
      "q[i] -= eta * g[i] / (G[i] + eps);", ["exact_recovery", "bruteforce_nnls_kkt"]),
+    ("adagrad_accumulates_magnitudes", "G[i] += g[i] * g[i];", "G[i] += fabs(g[i]);", ["one_adagrad_step"]),
+    ("adagrad_eps_under_the_root", "q[i] -= eta * g[i] / (sqrt(G[i]) + eps);",
+     "q[i] -= eta * g[i] / sqrt(G[i] + eps);", ["one_adagrad_step"]),
+    ("loss_sums_magnitudes", "loss += r[i] * r[i];", "loss += fabs(r[i]);", ["exact_recovery", "loss_grad_fd"]),
     ("adagrad_accumulates_after_step",
      "G[i] += g[i] * g[i];\n        q[i] -= eta * g[i] / (sqrt(G[i]) + eps);",
      "q[i] -= eta * g[i] / (sqrt(G[i]) + eps);\n        G[i] += g[i] * g[i];",
@@ -141,6 +160,10 @@ MUTANTS = [
      ["loss_grad_fd"]),
     ("dtheta_sign", "double dp = pk * (-d->Cc[(size_t)h * n->P + k] + mean_c);",
      "double dp = pk * (d->Cc[(size_t)h * n->P + k] - mean_c);", ["loss_grad_fd", "pattern_dtheta_fd"]),
+    ("dtheta_residual_of_departure_interval",
+     "gp[(size_t)x->h1 * n->P + x->k] += x->rho * r[(size_t)x->h2 * n->O + o];",
+     "gp[(size_t)x->h1 * n->P + x->k] += x->rho * r[(size_t)x->h1 * n->O + o];",
+     ["loss_grad_fd", "pattern_dtheta_fd"]),
     ("dtheta_mean_over_all_routes",
      "if (n->rod[k2] == od) mean_c += d->p[(size_t)h * n->P + k2] * d->Cc[(size_t)h * n->P + k2];",
      "mean_c += d->p[(size_t)h * n->P + k2] * d->Cc[(size_t)h * n->P + k2];",
@@ -162,6 +185,9 @@ MUTANTS = [
     # quality check
     ("r2_mean_over_all_cells", "if (mask[i]) {\n            sum += counts[i];",
      "{\n            sum += counts[i];", ["r2"]),
+    ("r2_total_sum_of_squares_of_the_fit",
+     "if (mask[i]) ss_tot += ((double)counts[i] - mean) * ((double)counts[i] - mean);",
+     "if (mask[i]) ss_tot += (xhat[i] - mean) * (xhat[i] - mean);", ["r2"]),
     # Sec. 2.7: consecutive days coupled across midnight
     ("coupled_next_day_on_own_speeds", "if (rc == OR_OK && speed_next) rc = or_ticks(n, speed_next, d->ticks + NA);",
      "if (rc == OR_OK && speed_next) rc = or_ticks(n, speed_mph, d->ticks + NA);",
@@ -170,6 +196,8 @@ MUTANTS = [
      "xfull[2 * sO * i + c];", ["coupled_forward_long_day", "coupled_solve_long_day"]),
     ("coupled_gradient_misses_next_day", "if (i > 0) r[2 * sO * (i - 1) + sO + c] = v;", "",
      ["coupled_solve_long_day", "coupled_loss_grad_fd"]),
+    ("coupled_gradient_without_factor_two", "for (size_t c = 0; c < sK; ++c) dq[sK * i + c] *= 2.0;", "",
+     ["coupled_loss_grad_fd"]),
     ("coupled_dar_cut_at_midnight", "h2 <= (hi - 1) / ipt && h2 < Nh; ++h2)",
      "h2 <= (hi - 1) / ipt && h2 < n->N; ++h2)", ["coupled_dar_mass", "coupled_forward_long_day"]),
     ("coupled_days_left_independent",

@@ -339,6 +339,24 @@ def test_spgd_reaches_bruteforce_nnls_and_kkt():
     np.testing.assert_allclose(q_star, q_ls, atol=1e-8)
 
 
+def test_one_adagrad_step_closed_form():
+    # Algorithm 1 from q0 = 0, G0 = 0: g = B^T (B 0 - x) = -B^T x, then G1 = g^2 and
+    # q1 = max(q0 - eta g / (sqrt(G1) + eps), 0) = eta |g| / (|g| + eps) where g < 0, 0 where
+    # g >= 0.  Counts with negative entries make some g positive (the projection acts), and a
+    # large eps shows where eps enters.
+    w, day, q_true, counts = _tiny_instance(noise=0.3, seed=5)
+    counts = counts.copy()
+    counts[:, :2] -= 25.0
+    mask = np.ones_like(counts, np.uint8)
+    g = -(day.dense_B().T @ counts.astype(np.float64).ravel())
+    assert np.any(g > 0) and np.any(g < 0)
+    for eps in [1e-10, 0.5]:
+        q, G, _ = day.solve(counts, mask, iters=1, eta=0.7, eps=eps)
+        np.testing.assert_allclose(G.ravel(), g * g, rtol=1e-13)
+        want = np.where(g < 0, 0.7 * -g / (np.abs(g) + eps), 0.0)
+        np.testing.assert_allclose(q.ravel(), want, rtol=1e-13, atol=0)
+
+
 def test_masked_rows_do_not_count():
     w, day, q_true, counts = _tiny_instance(noise=0.1)
     mask = np.ones_like(counts, np.uint8)
