@@ -14,6 +14,9 @@ Two kinds of change no pin can see, because they change no result:
   so the iterates do not change, up to the eps in the denominator;
 - leaving the last coupled day's next-day residual rows unset. That day's
   horizon ends at its midnight, so its B never reads them.
+A third is invisible in practice: the tie-break of the row order. Rows sort
+by 64-bit keys, and two keys of one day and epoch are equal with probability
+about n^2 / 2^65.
 
 Mutations are chosen to keep every memory access in bounds, so a mutant fails
 an assertion instead of crashing the test process.
@@ -54,6 +57,9 @@ PINS = {
     "one_adagrad_step": pp.test_one_adagrad_step_closed_form,
     "masked_rows_in_chunks": pp.test_masked_rows_do_not_count_in_row_chunks,
     "one_chunk_equals_full_batch": pp.test_row_chunk_covering_all_rows_equals_full_batch,
+    "row_chunk_epochs": pp.test_row_chunk_epochs_are_masked_full_row_steps_in_permuted_order,
+    "loss_trace": pp.test_loss_trace_is_the_loss_at_each_epoch_start,
+    "multi_day_driver": pp.test_multi_day_driver_runs_each_day_on_its_own_inputs,
     "row_chunks_converge": pp.test_row_chunks_converge_to_nnls,
     "loss_grad_fd": pp.test_loss_grad_matches_central_differences,
     "splitmix64_vectors": pp.test_splitmix64_published_vectors,
@@ -174,6 +180,23 @@ MUTANTS = [
      ["one_chunk_equals_full_batch"]),
     ("chunks_drawn_from_masked_rows", "if (mask[i]) order[n_obs_rows++] = (int32_t)i;",
      "order[n_obs_rows++] = (int32_t)i;", ["masked_rows_in_chunks"]),
+    ("chunks_one_row_short", "int32_t t = s + row_chunk < n_obs_rows ? s + row_chunk : n_obs_rows;",
+     "int32_t t = s + row_chunk - 1 < n_obs_rows ? s + row_chunk - 1 : n_obs_rows;", ["row_chunk_epochs"]),
+    ("chunked_loss_trace_not_recorded",
+     "if (loss_trace) {\n            or_forward(d, q, xhat);\n            loss_trace[e] = or_residual(d, xhat, counts, mask, r);\n        }",
+     "", ["loss_trace"]),
+    # the multi-day drivers
+    ("days_share_the_first_days_choice_times",
+     "if (choice_times) or_day_set_choice_times(d, choice_times + (size_t)n->N * n->P * i);",
+     "if (choice_times) or_day_set_choice_times(d, choice_times);", ["multi_day_driver"]),
+    ("day_ids_ignored", "day_ids ? day_ids[i] : i, q_inout", "i, q_inout", ["multi_day_driver"]),
+    ("forward_days_on_the_first_days_speeds",
+     "or_day *d = or_day_build(n, speeds + sA * i, theta, &err);\n        if (!d) {\n#ifdef _OPENMP\n"
+     "#pragma omp critical\n#endif\n            { if (status == OR_OK) status = err; }\n            continue;\n"
+     "        }\n        or_forward(",
+     "or_day *d = or_day_build(n, speeds, theta, &err);\n        if (!d) {\n#ifdef _OPENMP\n"
+     "#pragma omp critical\n#endif\n            { if (status == OR_OK) status = err; }\n            continue;\n"
+     "        }\n        or_forward(", ["multi_day_driver"]),
     ("splitmix64_shift", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;",
      "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;", ["splitmix64_vectors"]),
     ("splitmix64_indexed_off_by_one", "uint64_t st = s + i * 0x9E3779B97F4A7C15ULL;",

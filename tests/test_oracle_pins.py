@@ -397,6 +397,62 @@ def test_row_chunks_converge_to_nnls():
     np.testing.assert_allclose(q, q_true, rtol=1e-5, atol=1e-5)
 
 
+def test_row_chunk_epochs_are_masked_full_row_steps_in_permuted_order():
+    # Algorithm 1 with b rows per update: each epoch orders the observed rows by the
+    # permutation (pinned above) and makes one update per run of b consecutive rows, the
+    # last run partial.  One update on a set of rows is one full-row step with the mask
+    # reduced to those rows.
+    w, day, q_true, counts = _tiny_instance(noise=0.1)
+    mask = np.ones_like(counts, np.uint8)
+    mask[0, 1] = 0
+    rows = np.flatnonzero(mask.ravel()).astype(np.int32)
+    b, seed, d = 5, 11, 3
+    assert rows.size % b != 0                       # a partial last run
+    q, G, _ = day.solve(counts, mask, iters=2, row_chunk=b, seed=seed, day=d)
+    qe, Ge = np.zeros_like(q), np.zeros_like(G)
+    for epoch in range(2):
+        order = orc.permute_rows(rows, seed=seed, day=d, epoch=epoch)
+        for s in range(0, order.size, b):
+            m = np.zeros(mask.size, np.uint8)
+            m[order[s:s + b]] = 1
+            qe, Ge, _ = day.solve(counts, m.reshape(mask.shape), iters=1, q0=qe, G0=Ge)
+    np.testing.assert_array_equal(q, qe)
+    np.testing.assert_array_equal(G, Ge)
+
+
+def test_loss_trace_is_the_loss_at_each_epoch_start():
+    w, day, q_true, counts = _tiny_instance(noise=0.1)
+    mask = np.ones_like(counts, np.uint8)
+    for b in [0, 5]:
+        _, _, _, tr = day.solve(counts, mask, iters=4, row_chunk=b, seed=2, trace=True)
+        for e in range(4):
+            assert tr[e] == day.solve(counts, mask, iters=e, row_chunk=b, seed=2)[2]
+
+
+def test_multi_day_driver_runs_each_day_on_its_own_inputs():
+    # day i of the multi-day drivers: its own speeds, counts, mask, route-choice times
+    # and day id (the row order's stream), as when the day is solved alone
+    w = synth.corridor_7day()
+    net = orc.Net.from_workload(w)
+    days = [1, 4]
+    sp = w.speeds(days)
+    counts = w.counts_from(net.forward_days(sp, w.q_true(days).astype(np.float64)), days)
+    mask = w.mask(days)
+    Cc = orc.pattern_choice_times(net, w.speeds([0, 1, 4]), [0, 0, -1])[1:]   # day 1 with day 0; day 4 alone
+    ids = np.array([7, 9], np.int32)
+    kw = dict(iters=3, row_chunk=500, seed=5)
+    q, G, loss = net.solve_days(sp, counts, mask, day_ids=ids, choice_times=Cc, n_threads=2, **kw)
+    x = net.forward_days(sp, q, n_threads=2)
+    for i in range(len(days)):
+        d = net.day(sp[i])
+        np.testing.assert_array_equal(x[i], d.forward(q[i]))
+        d.set_choice_times(Cc[i])
+        qi, Gi, li = d.solve(counts[i], mask[i], day=int(ids[i]), **kw)
+        np.testing.assert_array_equal(q[i], qi)
+        np.testing.assert_array_equal(G[i], Gi)
+        assert loss[i] == li
+
+
 def test_day_order_does_not_change_per_day_results():
     w = synth.corridor_7day()
     net = orc.Net.from_workload(w)
