@@ -208,6 +208,8 @@ MUTANTS = [
     # quality check
     ("r2_mean_over_all_cells", "if (mask[i]) {\n            sum += counts[i];",
      "{\n            sum += counts[i];", ["r2"]),
+    ("r2_defined_without_spread", "return ss_tot > 0.0 ? 1.0 - ss_res / ss_tot : NAN;",
+     "return 1.0 - ss_res / ss_tot;", ["r2"]),
     ("r2_total_sum_of_squares_of_the_fit",
      "if (mask[i]) ss_tot += ((double)counts[i] - mean) * ((double)counts[i] - mean);",
      "if (mask[i]) ss_tot += (xhat[i] - mean) * (xhat[i] - mean);", ["r2"]),
@@ -221,6 +223,14 @@ MUTANTS = [
      ["coupled_solve_long_day", "coupled_loss_grad_fd"]),
     ("coupled_gradient_without_factor_two", "for (size_t c = 0; c < sK; ++c) dq[sK * i + c] *= 2.0;", "",
      ["coupled_loss_grad_fd"]),
+    ("coupled_dtheta_on_the_first_days_demand", "const double term = 2.0 * q[sK * i + (size_t)h * n->K + od]",
+     "const double term = 2.0 * q[(size_t)h * n->K + od]", ["coupled_loss_grad_fd"]),
+    ("coupled_dtheta_misses_next_day_rows",
+     "gp[(size_t)x->h1 * n->P + x->k] += x->rho * ri[(size_t)x->h2 * n->O + o];",
+     "if (x->h2 < n->N) gp[(size_t)x->h1 * n->P + x->k] += x->rho * ri[(size_t)x->h2 * n->O + o];",
+     ["coupled_loss_grad_fd"]),
+    ("coupled_loss_counts_rows_twice", "l += v * v;", "l += (i > 0 ? 2.0 : 1.0) * v * v;",
+     ["coupled_solve_long_day", "coupled_loss_grad_fd"]),
     ("coupled_dar_cut_at_midnight", "h2 <= (hi - 1) / ipt && h2 < Nh; ++h2)",
      "h2 <= (hi - 1) / ipt && h2 < n->N; ++h2)", ["coupled_dar_mass", "coupled_forward_long_day"]),
     ("coupled_days_left_independent",
