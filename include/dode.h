@@ -184,6 +184,7 @@ int dode_set_counts(dode_ctx *ctx, const float *counts, const uint8_t *mask, int
  * day_base + index in the loaded set; rows go in ascending (key, r)) and
  * makes one update per run of b consecutive rows (the last run partial);
  * the loss trace still reports the full masked loss at each epoch start.
+ * iters = 0 takes no step: q_out is the current state and loss_out its loss.
  * Errors: DODE_ERR_STATE (no days loaded), DODE_ERR_ARG, DODE_ERR_UNSUPPORTED
  * (row_chunk > 0 with the plain form), DODE_ERR_CUDA.
  */
