@@ -122,10 +122,10 @@ typedef struct {
                                 midnight as the per-day problem does.  Needs the fused form and
                                 row_chunk = 0 (else dode_create returns DODE_ERR_ARG), and a
                                 network whose accumulator ring and tick window fit in shared
-                                memory (else DODE_ERR_UNSUPPORTED at the first evaluation).  Each epoch then takes two launches; use_graph is
-                                ignored.  dode_dar_distance, dode_get_dar and
-                                dode_loss_static_scratch refuse coupled days.  0 = independent
-                                days (default). */
+                                memory (else DODE_ERR_UNSUPPORTED at the first evaluation).
+                                Each epoch then takes two launches; use_graph is ignored.
+                                dode_dar_distance, dode_get_dar and dode_loss_static_scratch
+                                refuse coupled days.  0 = independent days (default). */
 } dode_options;
 
 typedef struct dode_ctx dode_ctx;
