@@ -45,3 +45,29 @@ def test_algorithmic_bytes_of_the_3yr_corridor():
     import bench
     # counts 4*288*400 + mask 288*400/8 + ticks 2*288*438 + q 8*288*150 + G 8*288*150 + 8
     assert bench.algorithmic_bytes(288, 400, 438, 150) == 460800 + 14400 + 252288 + 345600 + 345600 + 8
+
+
+def test_measured_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
+    """The ncu figures are reported only for the workload, precision and kernel
+    source they were taken of (the source matched by its hash)."""
+    import hashlib
+
+    import bench
+    src = tmp_path / "paper_1901_09266_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    kernel = b"// a kernel source\n"
+    (src / "fused.cu").write_bytes(kernel)
+    (tmp_path / "profiles" / "fused_kernel_corridor-3yr-152d_traffic.txt").write_text(
+        "# a capture\n"
+        "kernel = k_fused<1,1,1> (BF16 form)\n"
+        f"fused_cu_sha256_16 = {hashlib.sha256(kernel).hexdigest()[:16]}\n"
+        "bytes_per_day_iteration = 4398377\n"
+        "warp_instructions_per_day_iteration = 3304333\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("corridor-3yr", "bf16") == 4398377.0
+    assert bench.measured_traffic("corridor-3yr", "bf16", "warp_instructions_per_day_iteration") == 3304333.0
+    assert bench.measured_traffic("corridor-3yr", "fp32") is None
+    assert bench.measured_traffic("corridor-large", "bf16") is None
+    (src / "fused.cu").write_bytes(kernel + b"// changed\n")
+    assert bench.measured_traffic("corridor-3yr", "bf16") is None
