@@ -71,3 +71,33 @@ def test_measured_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
     assert bench.measured_traffic("corridor-large", "bf16") is None
     (src / "fused.cu").write_bytes(kernel + b"// changed\n")
     assert bench.measured_traffic("corridor-3yr", "bf16") is None
+
+
+def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):
+    """The sampler's parsing, against a fake nvidia-smi that prints three samples
+    (one with the power cap active) and a malformed line."""
+    import time
+
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '2070, 2070, 1400.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo 'not a sample'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ.get('PATH', '')}")
+    s = bench.ClockSampler()
+    s.start()
+    t0 = time.time()
+    while len(s.lines) < 4 and time.time() - t0 < 10:
+        time.sleep(0.05)
+    r = s.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    empty = tmp_path / "empty"
+    empty.mkdir()
+    monkeypatch.setenv("PATH", str(empty))
+    s = bench.ClockSampler()
+    s.start()
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
