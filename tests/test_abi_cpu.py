@@ -140,3 +140,24 @@ def test_validation_rejects_routes_longer_than_64_links(lib):
         dode.Context(**args).close()
     except dode.DodeError as e:
         assert e.code != dode.ERR_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without the CUDA library the binding raises."""
+    monkeypatch.setattr(dode, "_lib", None)
+    with pytest.raises(ImportError):
+        dode.load(str(tmp_path / "libdode.so"))
+
+
+def test_product_never_reaches_the_oracle():
+    """The package neither imports the oracle nor loads its library."""
+    pkg = os.path.join(ROOT, "paper_1901_09266_gb300")
+    seen = 0
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                seen += 1
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
+                assert "liboracle" not in text and "dode_oracle" not in text and "or_solve" not in text, f
+    assert seen >= 10
