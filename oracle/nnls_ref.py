@@ -14,6 +14,7 @@ import numpy as np
 
 
 def nnls_bruteforce(B: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """The minimiser of Eq. (nnls) by enumerating supports (module docstring)."""
     n = B.shape[1]
     assert n <= 16, "support enumeration is exponential"
     best, best_loss = np.zeros(n), float(x @ x)

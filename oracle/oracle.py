@@ -25,6 +25,7 @@ _u8p = ct.POINTER(ct.c_uint8)
 
 
 def lib():
+    """The oracle library, built on first use."""
     global _lib
     if _lib is None:
         _lib = bind(_build.build())
@@ -101,6 +102,7 @@ def _c(a, dtype) -> np.ndarray:
 
 
 class OracleError(RuntimeError):
+    """A non-zero status of the oracle library (bad speed, tick overflow, ...)."""
     pass
 
 
@@ -126,6 +128,7 @@ class Net:
 
     @classmethod
     def from_workload(cls, w) -> "Net":
+        """The network and routes of a synthetic workload."""
         return cls(w.n_intervals, w.interval_s, w.ticks_per_s, w.net.link_len_mi, w.routes.route_ptr,
                    w.routes.route_links, w.routes.route_od, w.routes.n_od, w.net.obs_links)
 
@@ -135,6 +138,7 @@ class Net:
             self.h = None
 
     def day(self, speeds: np.ndarray, theta: float = 0.1) -> "Day":
+        """One day's model from its link speeds [N][A] (mph)."""
         return Day(self, speeds, theta)
 
     # ---- multi-day drivers -------------------------------------------
@@ -158,6 +162,7 @@ class Net:
         return q, G, loss
 
     def forward_days(self, speeds, q, theta=0.1, n_threads=1) -> np.ndarray:
+        """xhat [D][N][O] = B_d q_d for each day (Eq. (reverse) with Eq. (flow)), days independent."""
         D = speeds.shape[0]
         sp, qq = _c(speeds, np.float32), _c(q, np.float64)
         x = np.zeros((D, self.N, self.O))
@@ -243,6 +248,7 @@ class Day:
             self.h = None
 
     def set_theta(self, theta: float) -> None:
+        """Logit dispersion per minute of Eq. (logit); recomputes p and B."""
         self._L.or_day_set_theta(self.h, theta)
 
     def set_choice_times(self, Cc) -> None:
@@ -255,9 +261,11 @@ class Day:
 
     @property
     def n_repairs(self) -> int:
+        """FIFO repairs applied to the trajectories (Sec. 2.2)."""
         return int(self._L.or_day_repairs(self.h))
 
     def ticks(self) -> np.ndarray:
+        """Link travel times [N][A] in ticks by entry interval (Sec. 2.4)."""
         out = np.zeros((self.net.N, self.net.A), np.int32)
         self._L.or_day_get_ticks(self.h, _p(out, _i32p))
         return out
@@ -292,18 +300,21 @@ class Day:
         return C, p
 
     def B_coo(self):
+        """Assignment matrix of Eq. (assign) in COO: (row h2 * O + o, column h1 * K + od, value)."""
         m = int(self._L.or_day_nnz(self.h))
         r, c, v = np.zeros(m, np.int32), np.zeros(m, np.int32), np.zeros(m)
         self._L.or_day_get_B(self.h, _p(r, _i32p), _p(c, _i32p), _p(v, _f64p))
         return r, c, v
 
     def dense_B(self) -> np.ndarray:
+        """Dense assignment matrix [N * O][N * K] of Eq. (assign), for tiny instances."""
         n = self.net
         Bd = np.zeros((n.N * n.O, n.N * n.K))
         self._L.or_day_dense_B(self.h, _p(Bd, _f64p))
         return Bd
 
     def forward(self, q: np.ndarray) -> np.ndarray:
+        """xhat [N][O] = B q (Eq. (reverse) with Eq. (flow))."""
         n = self.net
         qq = _c(q, np.float64).reshape(n.N, n.K)
         x = np.zeros((n.N, n.O))
@@ -311,6 +322,7 @@ class Day:
         return x
 
     def adjoint(self, r: np.ndarray) -> np.ndarray:
+        """g [N][K] = B^T r (Algorithm 1's gradient without the factor 2)."""
         n = self.net
         rr = _c(r, np.float64).reshape(n.N, n.O)
         g = np.zeros((n.N, n.K))
@@ -318,6 +330,7 @@ class Day:
         return g
 
     def residual(self, xhat, counts, mask):
+        """(r = m (xhat - x), sum r^2) of Eq. (nnls)."""
         n = self.net
         xx, cc, mm = _c(xhat, np.float64), _c(counts, np.float32), _c(mask, np.uint8)
         r = np.zeros((n.N, n.O))
@@ -326,6 +339,8 @@ class Day:
 
     def solve(self, counts, mask, iters=200, eta=5.0, eps=1e-10, row_chunk=0, seed=0, day=0,
               q0=None, G0=None, trace=False):
+        """Algorithm 1 on this day: `iters` epochs from (q0, G0) (default 0), full-row updates or
+        runs of `row_chunk` permuted observed rows; (q, G, final loss[, loss at each epoch start])."""
         n = self.net
         cc, mm = _c(counts, np.float32), _c(mask, np.uint8)
         q = np.zeros((n.N, n.K)) if q0 is None else _c(q0, np.float64).copy()
@@ -393,6 +408,7 @@ def dar_distance(net: "Net", speeds: np.ndarray):
 
 
 def splitmix64(seed: int, n: int) -> list:
+    """The first n outputs of SplitMix64 (Steele, Lea and Flood 2014) from ``seed``."""
     st = ct.c_uint64(seed)
     return [int(lib().or_splitmix64_next(ct.byref(st))) for _ in range(n)]
 
@@ -403,6 +419,8 @@ def splitmix64_at(state: int, i: int) -> int:
 
 
 def permute_rows(rows: np.ndarray, seed: int, day: int, epoch: int) -> np.ndarray:
+    """Algorithm 1's permutate over the observed rows of one day and epoch (rows sorted by
+    their SplitMix64 keys)."""
     r = _c(rows, np.int32).copy()
     lib().or_permute_rows(_p(r, _i32p), r.size, ct.c_uint64(seed), day, epoch)
     return r
