@@ -21,6 +21,7 @@ from .dode import Context
 
 
 class DodeLoss(torch.autograd.Function):
+    """L(q, theta) of the loaded days as a torch autograd function (see the module docstring)."""
     @staticmethod
     def forward(fctx, q: torch.Tensor, theta: torch.Tensor, ctx: Context) -> torch.Tensor:
         if not q.is_cuda:

@@ -28,6 +28,7 @@ def _nvcc() -> str:
 
 
 def sources() -> list:
+    """The CUDA translation units of the library."""
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
@@ -40,6 +41,7 @@ def _stale(lib: str) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile every translation unit for sm_103a and link libdode.so; returns its path."""
     if not force and not _stale(LIB):
         return LIB
     os.makedirs(OBJ, exist_ok=True)

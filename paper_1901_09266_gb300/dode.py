@@ -36,23 +36,27 @@ EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_cou
 
 
 class DodeError(RuntimeError):
+    """A negative status of a libdode call (``code`` is the DODE_ERR_* value)."""
     def __init__(self, code: int, msg: str):
         super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
         self.code = code
 
 
 class dode_network(ct.Structure):
+    """``dode_network`` of include/dode.h: the directed graph and its observed links (Sec. 4, Step 0)."""
     _fields_ = [("n_nodes", ct.c_int32), ("n_links", ct.c_int32), ("link_tail", ct.c_void_p),
                 ("link_head", ct.c_void_p), ("link_len_mi", ct.c_void_p), ("n_obs", ct.c_int32),
                 ("obs_links", ct.c_void_p)]
 
 
 class dode_routes(ct.Structure):
+    """``dode_routes`` of include/dode.h: the path sets in CSR form (Sec. 4, Step 0)."""
     _fields_ = [("n_od", ct.c_int32), ("n_routes", ct.c_int32), ("route_od", ct.c_void_p),
                 ("route_ptr", ct.c_void_p), ("route_links", ct.c_void_p)]
 
 
 class dode_options(ct.Structure):
+    """``dode_options`` of include/dode.h."""
     _fields_ = [("n_intervals", ct.c_int32), ("interval_s", ct.c_int32), ("ticks_per_s", ct.c_int32),
                 ("theta_per_min", ct.c_float), ("eps", ct.c_float), ("row_chunk", ct.c_int32),
                 ("seed", ct.c_uint64), ("form", ct.c_int32), ("precision", ct.c_int32),
@@ -113,6 +117,7 @@ def load(path: str = LIB_PATH):
 
 
 def default_options() -> dode_options:
+    """``dode_default_options``: N = 288, 300 s intervals, 16 ticks/s, theta 0.1/min, eps 1e-10."""
     o = dode_options()
     load().dode_default_options(ct.byref(o))
     return o
@@ -153,6 +158,7 @@ class Context:
 
     @classmethod
     def from_workload(cls, w, **opt_fields) -> "Context":
+        """A context for a synthetic workload's network and routes; keyword options override defaults."""
         o = default_options()
         o.n_intervals, o.interval_s, o.ticks_per_s = w.n_intervals, w.interval_s, w.ticks_per_s
         for k, v in opt_fields.items():
@@ -161,6 +167,7 @@ class Context:
                    w.routes.n_od, w.routes.route_od, w.routes.route_ptr, w.routes.route_links, o)
 
     def close(self) -> None:
+        """``dode_destroy``: frees the context's device memory."""
         if getattr(self, "h", None):
             load().dode_destroy(self.h)
             self.h = None
@@ -199,11 +206,13 @@ class Context:
         return ks.pop() if ks else PTR_HOST
 
     def use_torch_stream(self) -> None:
+        """Issue the context's work on torch's current CUDA stream (``dode_set_stream``)."""
         import torch
         self._check(load().dode_set_stream(self.h, ct.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
     # ---- days -------------------------------------------------------------
     def set_days(self, counts, speeds, mask=None) -> None:
+        """``dode_set_days``: counts / mask [D][N][O], speeds [D][N][A] (Sec. 4, Steps 1 and 4); resets q, G."""
         D = int(counts.shape[0])
         pc, kc, kc_ = self._ptr(counts, np.float32, (D, self.N, self.O))
         ps, ks, ks_ = self._ptr(speeds, np.float32, (D, self.N, self.A))
@@ -213,6 +222,7 @@ class Context:
         self.D = D
 
     def set_counts(self, counts, mask=None) -> None:
+        """``dode_set_counts``: new counts (and mask) for the loaded days; speeds and state kept."""
         pc, kc, kc_ = self._ptr(counts, np.float32, (self.D, self.N, self.O))
         pm, km, km_ = self._ptr(mask, np.uint8, (self.D, self.N, self.O))
         kind = self._same_kind((kc_, True), (km_, mask is not None))
@@ -231,23 +241,27 @@ class Context:
         return q, loss
 
     def loss_trace(self, iters: int) -> np.ndarray:
+        """``dode_get_loss_trace``: [iters][D] masked loss at the start of each epoch of the last solve."""
         t = np.empty((iters, self.D), np.float32)
         self._check(load().dode_get_loss_trace(self.h, t.ctypes.data, iters))
         return t
 
     def get_state(self):
+        """``dode_get_state``: (q, G), each [D][N][K] FP32."""
         q = np.empty((self.D, self.N, self.K), np.float32)
         G = np.empty_like(q)
         self._check(load().dode_get_state(self.h, q.ctypes.data, G.ctypes.data, PTR_HOST))
         return q, G
 
     def set_state(self, q, G) -> None:
+        """``dode_set_state``: replace the solver state (q, G)."""
         pq, _, kq = self._ptr(q, np.float32, (self.D, self.N, self.K))
         pg, _, kg = self._ptr(G, np.float32, (self.D, self.N, self.K))
         kind = self._same_kind((kq, q is not None), (kg, G is not None))
         self._check(load().dode_set_state(self.h, pq, pg, kind))
 
     def forward(self, q, xhat_out=None):
+        """``dode_forward``: xhat = B q per day (Eq. (reverse) with Eq. (flow))."""
         pq, _, kq = self._ptr(q, np.float32, (self.D, self.N, self.K))
         x = np.empty((self.D, self.N, self.O), np.float32) if xhat_out is None else xhat_out
         px, _, kx = self._ptr(x, np.float32, (self.D, self.N, self.O))
@@ -256,6 +270,7 @@ class Context:
         return x
 
     def loss(self, q, theta: Optional[float] = None) -> np.ndarray:
+        """``dode_loss``: per-day masked loss of Eq. (nnls) at q, for dispersion theta."""
         pq, _, kq = self._ptr(q, np.float32, (self.D, self.N, self.K))
         out = np.empty(self.D, np.float64)
         th = self.opt.theta_per_min if theta is None else theta
@@ -263,6 +278,7 @@ class Context:
         return out
 
     def loss_grad(self, q, theta: Optional[float] = None, dq_out=None):
+        """``dode_loss_grad``: (loss, dL/dq = 2 B^T r, dL/dtheta per day) through Eq. (logit)."""
         pq, _, kq = self._ptr(q, np.float32, (self.D, self.N, self.K))
         dq = np.empty((self.D, self.N, self.K), np.float32) if dq_out is None else dq_out
         pd, _, kd = self._ptr(dq, np.float32, (self.D, self.N, self.K))
@@ -315,21 +331,25 @@ class Context:
 
     # ---- inspection --------------------------------------------------------
     def ticks(self, day: int) -> np.ndarray:
+        """``dode_get_ticks``: [N][A] link travel times in ticks by entry interval (Sec. 2.4)."""
         out = np.empty((self.N, self.A), np.int32)
         self._check(load().dode_get_ticks(self.h, day, out.ctypes.data))
         return out
 
     def route_times(self, day: int) -> np.ndarray:
+        """``dode_get_route_times``: [N][P] route times in minutes (Eq. (cost))."""
         out = np.empty((self.N, self.P), np.float32)
         self._check(load().dode_get_route_times(self.h, day, out.ctypes.data))
         return out
 
     def day_info(self, day: int):
+        """``dode_get_day_info``: (FIFO repairs, largest trip offset in intervals)."""
         rep, off = ct.c_int64(0), ct.c_int32(0)
         self._check(load().dode_get_day_info(self.h, day, ct.byref(rep), ct.byref(off)))
         return rep.value, off.value
 
     def dar(self, day: int):
+        """``dode_get_dar``: (kjh [n][4] = (k, j, h1, h2), rho [n]) of Eq. (dar)."""
         n = ct.c_int64(0)
         self._check(load().dode_get_dar(self.h, day, ct.byref(n), None, None))
         kjh = np.empty((n.value, 4), np.int32)
@@ -338,15 +358,19 @@ class Context:
         return kjh, rho
 
     def last_kernel_ms(self) -> float:
+        """``dode_last_kernel_ms``: device time of the last call's hot-path kernels."""
         return float(load().dode_last_kernel_ms(self.h))
 
     def last_launches(self) -> int:
+        """``dode_last_launches``: hot-path kernel launches of the last call."""
         return int(load().dode_last_launches(self.h))
 
     def total_launches(self) -> int:
+        """``dode_total_launches``: all kernel launches of this context."""
         return int(load().dode_total_launches(self.h))
 
     def set_launch(self, block_threads: int, ctas_per_sm: int, max_ctas: int = 0) -> None:
+        """``dode_set_launch`` and ``dode_set_max_ctas``: the fused kernel's launch shape (0 = tuned)."""
         self._check(load().dode_set_launch(self.h, block_threads, ctas_per_sm))
         self.opt.max_ctas = max_ctas
         self._check(load().dode_set_max_ctas(self.h, max_ctas))
