@@ -38,6 +38,8 @@ if ROOT not in sys.path:
 # counts 4 N O + bit mask N O / 8 + uint16 tick table 2 N A + q read+write
 # 8 N K + Adagrad accumulator read+write 8 N K + per-day loss 8
 def algorithmic_bytes(N: int, O: int, A: int, K: int) -> int:
+    """Bytes one day-iteration must move at least: counts, mask bits, uint16 ticks, q and G read and
+    written, and the day's loss."""
     return 4 * N * O + (N * O) // 8 + 2 * N * A + 8 * N * K + 8 * N * K + 8
 
 
@@ -138,6 +140,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def dist_env():
+    """(world size, rank, local rank) from the torchrun environment; (1, 0, 0) without it."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -145,6 +148,7 @@ def dist_env():
 
 
 def dist_init(backend: str):
+    """Join the process group of a multi-rank run (127.0.0.1 rendezvous from the environment)."""
     import torch.distributed as dist
     if not dist.is_initialized():
         dist.init_process_group(backend=backend)
@@ -152,12 +156,14 @@ def dist_init(backend: str):
 
 
 def dist_barrier():
+    """Barrier across ranks; a no-op on one rank."""
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
         dist.barrier()
 
 
 def dist_max(x: float) -> float:
+    """The maximum of x over ranks."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()):
@@ -173,6 +179,7 @@ def dist_max(x: float) -> float:
 # ---------------------------------------------------------------------------
 
 def make_workload(name: str, n_days: int):
+    """The seeded synthetic workload called `name` with `n_days` days."""
     from paper_1901_09266_gb300 import synth
     if name == "corridor-3yr":
         return synth.corridor_3yr(n_days=n_days)
@@ -224,6 +231,7 @@ def oracle_rate(w, days, epochs: int, threads: int):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, unmodified, timed on the host cores on a bounded sample."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -257,6 +265,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 
 def run_gpu(args):
+    """This library's arm: the timed solve, end-to-end and comparison runs, one JSON line on rank 0."""
     import torch
     from paper_1901_09266_gb300 import build, dode, synth
 
@@ -541,6 +550,7 @@ def run_gpu(args):
 
 
 def main(argv=None):
+    """Parse the arguments and run one arm."""
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
