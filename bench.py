@@ -148,7 +148,8 @@ def dist_env():
 
 
 def dist_init(backend: str):
-    """Join the process group of a multi-rank run (127.0.0.1 rendezvous from the environment)."""
+    """Join the process group of a multi-rank run; the rendezvous address comes from the environment
+    (MASTER_ADDR / MASTER_PORT, set by torchrun)."""
     import torch.distributed as dist
     if not dist.is_initialized():
         dist.init_process_group(backend=backend)
