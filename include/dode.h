@@ -217,6 +217,19 @@ int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, flo
                    double *dtheta, int32_t ptr_kind);
 
 /*
+ * dode_last_totals -- the multi-year objective of Sec. 2.7 as the sum of the
+ * independent days' objectives: FP64 sums, in day order, of the per-day
+ * results of the context's last dode_loss or dode_loss_grad call, formed on
+ * the device.
+ *   loss_total    sum_d loss_d (host)
+ *   dtheta_total  sum_d dL_d/dtheta (host), may be NULL; needs dode_loss_grad
+ *                 as the last of the two calls
+ * Errors: DODE_ERR_STATE (no such call since the days were loaded, or
+ * dtheta_total after dode_loss), DODE_ERR_ARG, DODE_ERR_CUDA.
+ */
+int dode_last_totals(dode_ctx *ctx, double *loss_total, double *dtheta_total);
+
+/*
  * dode_dense_nnls -- the paper's efficiency experiment (Sec. 5, "Algorithm
  * efficiency": a dense random B, y = B x with x >= 0, NNLS(B, y)) solved by
  * Algorithm 1 with full-row updates, for m right-hand sides sharing B:
@@ -303,12 +316,15 @@ int dode_dar_distance(dode_ctx *ctx, double *dist, double *mean_sq);
  * loads this library holds until the process exits; the day data and route
  * tables are the context's, loaded earlier.  If the days need more scratch
  * than that for even one CTA the call returns DODE_ERR_ARG and says how much;
- * otherwise it runs as many resident CTAs as fit.  The first call on a device
- * looks up the array's device address there (cudaGetSymbolAddress), so that
- * first call should come before any stream capture.  Every call shares the
- * array and leaves its contents behind: calls that overlap on the GPU (on
- * different streams or contexts of the same device) race and must not be made.
- * Returns after the loss is written.
+ * otherwise it runs as many resident CTAs as fit (dode_last_grid reports how
+ * many).  Each call looks up the array's device address on the context's
+ * device (cudaGetSymbolAddress; host code only holds a stand-in under the
+ * array's name), so a device reset between calls leaves no stale address.  The
+ * call synchronises the context's stream, so it cannot be made while that
+ * stream is being captured.  Every call shares the array and leaves its
+ * contents behind: calls that overlap on the GPU (on different streams or
+ * contexts of the same device) race and must not be made.  Returns after the
+ * loss is written.
  */
 int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float theta, double *loss);
 
@@ -335,6 +351,10 @@ int dode_get_dar(dode_ctx *ctx, int32_t day, int64_t *n, int32_t *kjh, float *rh
 double dode_last_kernel_ms(const dode_ctx *ctx);
 /* Number of hot-path kernel launches the last solve / forward / loss call made. */
 int64_t dode_last_launches(const dode_ctx *ctx);
+/* CTAs of the last call's fused-kernel launch (0 if that call ran no fused kernel). */
+int32_t dode_last_grid(const dode_ctx *ctx);
+/* CUDA device ordinal the context runs on (-1 for a NULL context). */
+int32_t dode_device(const dode_ctx *ctx);
 /* Number of kernel launches (all kernels, all calls) made by this context so far. */
 int64_t dode_total_launches(const dode_ctx *ctx);
 /* Override the fused kernel launch shape (autotuner); 0 = tuned default. */

@@ -14,7 +14,6 @@ libdode; torch only provides device memory and the stream.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from .dode import Context
@@ -29,7 +28,8 @@ class DodeLoss(torch.autograd.Function):
         qc = q.detach().to(torch.float32).contiguous()
         th = float(theta.detach().cpu().item()) if isinstance(theta, torch.Tensor) else float(theta)
         ctx.use_torch_stream()
-        per_day = ctx.loss(qc, th)
+        ctx.loss(qc, th)
+        total, _ = ctx.last_totals()
         fctx.save_for_backward(qc)
         fctx.theta = th
         fctx.dctx = ctx
@@ -37,19 +37,21 @@ class DodeLoss(torch.autograd.Function):
         fctx.theta_dtype = theta.dtype if isinstance(theta, torch.Tensor) else torch.float64
         fctx.theta_device = theta.device if isinstance(theta, torch.Tensor) else torch.device("cpu")
         fctx.q_dtype = q.dtype
-        return torch.tensor(float(np.sum(per_day)), dtype=torch.float64, device=q.device)
+        return torch.tensor(total, dtype=torch.float64, device=q.device)
 
     @staticmethod
     def backward(fctx, grad_out: torch.Tensor):
         (qc,) = fctx.saved_tensors
         ctx: Context = fctx.dctx
         dq = torch.empty_like(qc)
-        _, _, dth = ctx.loss_grad(qc, fctx.theta, dq_out=dq)
+        ctx.loss_grad(qc, fctx.theta, dq_out=dq)
+        _, dth_total = ctx.last_totals(with_dtheta=True)
+        # chain rule: the upstream gradient scales the library's dL/dq and dL/dtheta
         g = grad_out.to(torch.float64)
         grad_q = (dq.to(torch.float64) * g).to(fctx.q_dtype)
         grad_theta = None
         if fctx.theta_is_tensor:
-            grad_theta = torch.tensor(float(g.item()) * float(np.sum(dth)), dtype=fctx.theta_dtype,
+            grad_theta = torch.tensor(float(g.item()) * dth_total, dtype=fctx.theta_dtype,
                                       device=fctx.theta_device)
         return grad_q, grad_theta, None
 

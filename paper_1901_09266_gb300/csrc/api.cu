@@ -8,7 +8,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -74,6 +73,8 @@ struct dode_ctx {
     float *d_q = nullptr, *d_G = nullptr, *d_qtmp = nullptr, *d_gout = nullptr, *d_xout = nullptr;
     __nv_bfloat16 *d_qb = nullptr;
     double *d_loss = nullptr, *d_dtheta = nullptr;
+    double *d_totals = nullptr;  // [2] cross-day totals (dode_last_totals)
+    int totals_kind = 0;         // what d_loss / d_dtheta hold: 0 nothing, 1 losses, 2 losses and dL/dtheta
     float *d_trace = nullptr;
     size_t trace_cap = 0;
     int trace_iters = -1;
@@ -101,6 +102,7 @@ struct dode_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0.0;
     int64_t last_launches = 0;
+    int32_t last_grid = 0;       // CTAs of the last fused-kernel launch
     int64_t total_launches = 0;
     // CUDA graph of dode_solve's device work (use_graph)
     cudaGraphExec_t graph_exec = nullptr;
@@ -601,6 +603,7 @@ int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
                             ctx->Np, ctx->d_pt, ctx->stream));
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
     ctx->last_launches = 1;
+    ctx->last_grid = s.grid;
     if (p.coupled) {
         // coupled days: every day's early rows and spill for this q first
         FusedParams ph = p;
@@ -646,6 +649,7 @@ int solve_coupled(dode_ctx *ctx, FusedParams p, int iters) {
     }
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     ctx->last_launches = 2LL * (iters + 1);
+    ctx->last_grid = s.grid;
     return DODE_OK;
 }
 
@@ -809,6 +813,7 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
     CU(cudaGraphLaunch(ctx->graph_exec, gs));
     if (gs != ctx->stream) CU(cudaStreamSynchronize(gs));
     ctx->last_launches = 1;
+    ctx->last_grid = s.grid;
     ctx->total_launches += kernels;
     return DODE_OK;
 }
@@ -849,6 +854,10 @@ const char *dode_last_error(const dode_ctx *ctx) { return ctx ? ctx->err.c_str()
 double dode_last_kernel_ms(const dode_ctx *ctx) { return ctx ? ctx->last_ms : 0.0; }
 
 int64_t dode_last_launches(const dode_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+int32_t dode_last_grid(const dode_ctx *ctx) { return ctx ? ctx->last_grid : 0; }
+
+int32_t dode_device(const dode_ctx *ctx) { return ctx ? ctx->dev : -1; }
 
 int64_t dode_total_launches(const dode_ctx *ctx) { return ctx ? ctx->total_launches : 0; }
 
@@ -988,6 +997,7 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
         cudaError_t e_ = (call);                                               \
         if (e_ != cudaSuccess) return bail(DODE_ERR_CUDA, cudaGetErrorString(e_)); \
     } while (0)
+    CUB(dalloc(&ctx->d_totals, 2));
     CUB(upload(&ctx->d_rptr, ctx->rptr, ctx->stream));
     CUB(upload(&ctx->d_rlinks, ctx->rlinks, ctx->stream));
     CUB(upload(&ctx->d_rod, ctx->rod, ctx->stream));
@@ -1029,6 +1039,7 @@ void dode_destroy(dode_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     free_days(ctx);
+    dfree(ctx->d_totals);
     dfree(ctx->d_rptr);
     dfree(ctx->d_rlinks);
     dfree(ctx->d_rod);
@@ -1114,6 +1125,7 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
         ctx->D = D;
     }
     ctx->plain_ready = false;
+    ctx->totals_kind = 0;
     ctx->trace_iters = -1;
     ctx->patterns = false;
     // speeds -> ticks (staged through the device when on the host)
@@ -1292,6 +1304,7 @@ int dode_solve(dode_ctx *ctx, int32_t iters, float step, int32_t batch, float *q
         }
         CU(cudaEventRecord(ctx->ev1, ctx->stream));
         ctx->last_launches = 1 + 3LL * iters + 2;
+        ctx->last_grid = 0;
         CU(cudaMemcpyAsync(ctx->d_loss, ctx->d_ptrace + (size_t)iters * D, D * sizeof(double),
                            cudaMemcpyDeviceToDevice, ctx->stream));
     } else {
@@ -1406,6 +1419,7 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
     if (!q || !loss || bad_ptr_kind(ptr_kind) || !std::isfinite(theta)) return fail(ctx, DODE_ERR_ARG, "loss arguments");
     int rc = fused_eval(ctx, MODE_LOSS, q, theta, ptr_kind);
     if (rc) return rc;
+    ctx->totals_kind = 1;
     CU(cudaMemcpyAsync(loss, ctx->d_loss, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     return DODE_OK;
@@ -1649,10 +1663,29 @@ int dode_loss_grad(dode_ctx *ctx, const float *q, float theta, double *loss, flo
         return fail(ctx, DODE_ERR_ARG, "loss_grad arguments");
     int rc = fused_eval(ctx, MODE_LOSS_GRAD, q, theta, ptr_kind);
     if (rc) return rc;
+    ctx->totals_kind = 2;
     if (dq && (rc = output_odmajor(ctx, ctx->d_gout, dq, ctx->K, 1.f, ptr_kind))) return rc;
     CU(cudaMemcpyAsync(loss, ctx->d_loss, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     if (dtheta) CU(cudaMemcpyAsync(dtheta, ctx->d_dtheta, ctx->D * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    return DODE_OK;
+}
+
+int dode_last_totals(dode_ctx *ctx, double *loss_total, double *dtheta_total) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (!loss_total) return fail(ctx, DODE_ERR_ARG, "last_totals: loss_total is NULL");
+    if (ctx->totals_kind == 0) return fail(ctx, DODE_ERR_STATE, "no loss or gradient call since the days were loaded");
+    if (dtheta_total && ctx->totals_kind != 2)
+        return fail(ctx, DODE_ERR_STATE, "dtheta_total needs a dode_loss_grad call as the last evaluation");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    CUL(launch_day_totals(ctx->d_loss, ctx->totals_kind == 2 ? ctx->d_dtheta : nullptr, ctx->D, ctx->d_totals,
+                          ctx->stream));
+    double h[2];
+    CU(cudaMemcpyAsync(h, ctx->d_totals, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *loss_total = h[0];
+    if (dtheta_total) *dtheta_total = h[1];
     return DODE_OK;
 }
 
@@ -1791,28 +1824,20 @@ int dode_get_dar(dode_ctx *ctx, int32_t day, int64_t *n, int32_t *kjh, float *rh
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)32 << 20;   // 32 MiB
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) unsigned char dode_static_scratch[kStaticScratchBytes];
-
-std::mutex g_static_scratch_mu;
-void *g_static_scratch_ptr[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Device address of the static scratch on the context's device: looked up
-// once per device (with that device current) and cached.
+// Device address of the static scratch on the context's device.  Host code
+// only holds a host-side stand-in under the array's name, so the address is
+// looked up with that device current -- on every call, which is cheap and
+// stays right if the process resets the device between calls.
 int static_scratch(dode_ctx *ctx, unsigned char **out) {
-    if (ctx->dev < 0 || ctx->dev >= kMaxDevices) return fail(ctx, DODE_ERR_ARG, "device ordinal above 63");
-    std::lock_guard<std::mutex> lock(g_static_scratch_mu);
-    if (!g_static_scratch_ptr[ctx->dev]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, dode_static_scratch);
-        if (e != cudaSuccess || !ptr)
-            return fail(ctx, DODE_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
-        g_static_scratch_ptr[ctx->dev] = ptr;
-    }
-    *out = static_cast<unsigned char *>(g_static_scratch_ptr[ctx->dev]);
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, dode_static_scratch);
+    if (e != cudaSuccess || !ptr)
+        return fail(ctx, DODE_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+    *out = static_cast<unsigned char *>(ptr);
     return DODE_OK;
 }
 
@@ -1885,6 +1910,7 @@ extern "C" int dode_loss_static_scratch(dode_ctx *ctx, const float *q, float the
     p.rtab_packed = sh.rtab_packed;
     p.queue = reinterpret_cast<int *>(base);
     CUL(launch_fused(p, prec, grid, sh.block, sh.smem, ctx->stream));
+    ctx->last_grid = grid;
     CU(cudaStreamSynchronize(ctx->stream));
     return check_device_error(ctx);
 }

@@ -217,6 +217,7 @@ cudaError_t fused_occupancy(int precision, int block, size_t smem, int *blocks_p
 cudaError_t fused_set_attr(bool smem_ring, bool smem_ticks, int precision, size_t smem);
 cudaError_t launch_r2(const float *counts, const uint32_t *mask, int D, int O, int N, int Np, int Nw,
                       const double *loss, double *sstot, double *r2, cudaStream_t s);
+cudaError_t launch_day_totals(const double *loss, const double *dth, int D, double *out, cudaStream_t s);
 cudaError_t launch_pattern_times(const float *C, int n_groups, const int32_t *gptr, const int32_t *gday, int P, int N,
                                  int Np, float *Ceff, cudaStream_t s);
 cudaError_t launch_dar_distance(const DarParams &p, double *part, int n_part, double *rbar_sq, double *dist,

@@ -135,4 +135,24 @@ cudaError_t launch_dar_distance(const DarParams &p, double *part, int n_part, do
     return cudaGetLastError();
 }
 
+// Cross-day totals of the per-day results (Sec. 2.7: the multi-year objective
+// is the sum of the independent days' objectives): FP64 sums in day order, by
+// one thread, so that the total does not depend on any launch shape.
+__global__ void k_day_totals(const double *__restrict__ loss, const double *__restrict__ dth, int D,
+                             double *__restrict__ out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double l = 0.0, t = 0.0;
+    for (int d = 0; d < D; ++d) {
+        l += loss[d];
+        if (dth) t += dth[d];
+    }
+    out[0] = l;
+    out[1] = t;
+}
+
+cudaError_t launch_day_totals(const double *loss, const double *dth, int D, double *out, cudaStream_t s) {
+    k_day_totals<<<1, 32, 0, s>>>(loss, dth, D, out);
+    return cudaGetLastError();
+}
+
 }  // namespace dode

@@ -30,8 +30,8 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 # every entry point of include/dode.h
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
-           "dode_loss_grad", "dode_dense_nnls", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
-           "dode_last_kernel_ms", "dode_last_launches", "dode_total_launches", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
+           "dode_loss_grad", "dode_last_totals", "dode_dense_nnls", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
+           "dode_last_kernel_ms", "dode_last_launches", "dode_last_grid", "dode_total_launches", "dode_device", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "dode_forward": (ct.c_int, [vp, vp, vp, i32]),
         "dode_loss": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_loss_grad": (ct.c_int, [vp, vp, f32, vp, vp, vp, i32]),
+        "dode_last_totals": (ct.c_int, [vp, vp, vp]),
         "dode_dense_nnls": (ct.c_int, [i32, i32, i32, vp, vp, i32, f32, f32, i32, vp, vp, vp, vp, i32, vp]),
         "dode_set_patterns": (ct.c_int, [vp, vp]),
         "dode_r2": (ct.c_int, [vp, vp, f32, vp, i32]),
@@ -101,6 +102,8 @@ def load(path: str = LIB_PATH):
         "dode_get_dar": (ct.c_int, [vp, i32, ct.POINTER(i64), vp, vp]),
         "dode_last_kernel_ms": (f64, [vp]),
         "dode_last_launches": (i64, [vp]),
+        "dode_last_grid": (i32, [vp]),
+        "dode_device": (i32, [vp]),
         "dode_total_launches": (i64, [vp]),
         "dode_set_launch": (ct.c_int, [vp, i32, i32]),
         "dode_set_max_ctas": (ct.c_int, [vp, i32]),
@@ -131,6 +134,25 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+# the torch dtype a device array must have, by the numpy dtype the entry point expects
+_TORCH_DTYPE_NAMES = {np.dtype(np.float32): "float32", np.dtype(np.float64): "float64",
+                      np.dtype(np.uint8): "uint8", np.dtype(np.int32): "int32"}
+
+
+def _check_torch(x, dtype, device: Optional[int], what: str = "tensor") -> None:
+    """Reject a torch tensor the library cannot take as a device array of numpy dtype ``dtype``:
+    not on CUDA, not contiguous, of another element type (the kernels would read or write past
+    its end), or on another GPU than ``device`` (None: any)."""
+    import torch
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError(f"{what}: torch tensors must be contiguous CUDA tensors")
+    want = getattr(torch, _TORCH_DTYPE_NAMES[np.dtype(dtype)])
+    if x.dtype != want:
+        raise ValueError(f"{what}: dtype {x.dtype}, expected {want}")
+    if device is not None and x.device.index != device:
+        raise ValueError(f"{what}: tensor on cuda:{x.device.index}, the context runs on cuda:{device}")
+
+
 class Context:
     """One ``dode_ctx``: network + routes, the loaded days and the solver state."""
 
@@ -155,6 +177,7 @@ class Context:
             raise DodeError(rc, "dode_create failed (details on stderr)")
         self.h = h
         self.D = 0
+        self.device = int(L.dode_device(h))
 
     @classmethod
     def from_workload(cls, w, **opt_fields) -> "Context":
@@ -188,8 +211,7 @@ class Context:
         if x is None:
             return None, None, PTR_HOST
         if _is_torch(x):
-            if not x.is_cuda or not x.is_contiguous():
-                raise ValueError("torch tensors must be contiguous CUDA tensors")
+            _check_torch(x, dtype, self.device)
             if shape is not None and tuple(x.shape) != tuple(shape):
                 raise ValueError(f"shape {tuple(x.shape)} != {tuple(shape)}")
             return x.data_ptr(), x, PTR_DEVICE
@@ -289,6 +311,14 @@ class Context:
         self._check(load().dode_loss_grad(self.h, pq, th, loss.ctypes.data, pd, dth.ctypes.data, kind))
         return loss, dq, dth
 
+    def last_totals(self, with_dtheta: bool = False):
+        """``dode_last_totals``: (sum of the last call's per-day losses, sum of its dL/dtheta or None),
+        FP64 in day order, summed by the library."""
+        lt = np.zeros(1, np.float64)
+        tt = np.zeros(1, np.float64)
+        self._check(load().dode_last_totals(self.h, lt.ctypes.data, tt.ctypes.data if with_dtheta else None))
+        return float(lt[0]), (float(tt[0]) if with_dtheta else None)
+
     def set_patterns(self, pattern=None) -> None:
         """Traffic pattern label of each loaded day (-1 = own travel times);
         None clears them.  Route choice then uses each pattern's mean times."""
@@ -365,6 +395,10 @@ class Context:
         """``dode_last_launches``: hot-path kernel launches of the last call."""
         return int(load().dode_last_launches(self.h))
 
+    def last_grid(self) -> int:
+        """``dode_last_grid``: CTAs of the last call's fused-kernel launch."""
+        return int(load().dode_last_grid(self.h))
+
     def total_launches(self) -> int:
         """``dode_total_launches``: all kernel launches of this context."""
         return int(load().dode_total_launches(self.h))
@@ -386,6 +420,11 @@ def dense_nnls(B, Y, iters: int, step: float, X0=None, G0=None, eps: float = 1e-
     dev = _is_torch(B)
     if dev:
         import torch
+        for name, t in (("B", B), ("Y", Y), ("X0", X0), ("G0", G0)):
+            if t is not None:
+                if not _is_torch(t):
+                    raise ValueError(f"{name}: mix of host and device arrays in one call")
+                _check_torch(t, np.float32, B.device.index, name)
         nr, nc = B.shape
         m = Y.shape[1]
         X = torch.zeros((nc, m), dtype=torch.float32, device=B.device) if X0 is None else X0

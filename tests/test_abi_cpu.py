@@ -161,3 +161,43 @@ def test_product_never_reaches_the_oracle():
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), f
                 assert "liboracle" not in text and "dode_oracle" not in text and "or_solve" not in text, f
     assert seen >= 10
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA torch tensor on a machine without a GPU: the
+    binding's marshalling reads only these attributes."""
+    __module__ = "torch.fake"
+
+    def __init__(self, shape, dtype, index=0, contiguous=True):
+        self.shape, self.dtype, self.is_cuda = tuple(shape), dtype, True
+        self.device = type("Dev", (), {"index": index})()
+        self._c = contiguous
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        return 0x1000
+
+
+def test_binding_rejects_device_arrays_of_the_wrong_dtype_or_gpu():
+    # a float32 loss buffer would take 8 D bytes of FP64 writes into 4 D bytes,
+    # a float16 q would be read past its end: both are refused before any call
+    torch = pytest.importorskip("torch")
+    ctx = object.__new__(dode.Context)
+    ctx.device = 0
+    D, N, K = 3, 288, 30
+    ok_q = _FakeCudaTensor((D, N, K), torch.float32)
+    assert ctx._ptr(ok_q, np.float32, (D, N, K))[2] == dode.PTR_DEVICE
+    with pytest.raises(ValueError, match="dtype"):
+        ctx._ptr(_FakeCudaTensor((D,), torch.float32), np.float64, (D,))
+    with pytest.raises(ValueError, match="dtype"):
+        ctx._ptr(_FakeCudaTensor((D, N, K), torch.float16), np.float32, (D, N, K))
+    with pytest.raises(ValueError, match="dtype"):
+        ctx._ptr(_FakeCudaTensor((D, N, K), torch.bfloat16), np.float32, (D, N, K))
+    with pytest.raises(ValueError, match="cuda:1"):
+        ctx._ptr(_FakeCudaTensor((D, N, K), torch.float32, index=1), np.float32, (D, N, K))
+    with pytest.raises(ValueError, match="contiguous"):
+        ctx._ptr(_FakeCudaTensor((D, N, K), torch.float32, contiguous=False), np.float32, (D, N, K))
+    with pytest.raises(ValueError, match="shape"):
+        ctx._ptr(_FakeCudaTensor((D, N, K + 1), torch.float32), np.float32, (D, N, K))

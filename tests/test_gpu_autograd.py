@@ -46,6 +46,8 @@ def test_autograd_matches_oracle_and_finite_differences():
         dabs_tot += dabs
         assert rel_norm(q.grad[d].cpu().numpy(), dqo) < 1e-4
     assert float(L.detach()) == pytest.approx(lo_tot, rel=1e-5)
+    print(f"autograd dtheta: sum|terms| / |dtheta| = {dabs_tot / abs(dth_tot):.1f}, "
+          f"relative error {abs(float(theta.grad) - dth_tot) / abs(dth_tot):.2e}")
     assert abs(float(theta.grad) - dth_tot) <= 1e-5 * dabs_tot
     # central differences (h = 1e-3) of the GPU loss itself
     h = 1e-3
@@ -112,3 +114,30 @@ def test_large_corridor_all_days_sampled_gradients():
         assert loss[d] == pytest.approx(lo, rel=1e-5)
         assert rel_norm(dq[d], dqo) < 1e-4
         assert abs(dth[d] - dtho) <= 1e-5 * dabs
+
+
+def test_last_totals_are_day_order_sums():
+    """dode_last_totals: the FP64 day-order sums of the per-day results, formed
+    by the library (the cross-day reduction the autograd wrapper returns)."""
+    w = synth.corridor_7day()
+    days = list(range(w.n_days))
+    net, sp, counts, mask, ctx = _setup(w, days)
+    q0 = w.q_true().astype(np.float32)
+    with pytest.raises(dode.DodeError):
+        ctx.last_totals()                                # nothing evaluated yet
+    loss = ctx.loss(q0, 0.1)
+    tot, none = ctx.last_totals()
+    assert none is None
+    seq = 0.0
+    for v in loss:                                       # day order, FP64
+        seq += float(v)
+    assert tot == seq
+    with pytest.raises(dode.DodeError):
+        ctx.last_totals(with_dtheta=True)                # the last call has no dL/dtheta
+    loss, _, dth = ctx.loss_grad(q0, 0.1)
+    tot, tth = ctx.last_totals(with_dtheta=True)
+    seq_l = seq_t = 0.0
+    for a, b in zip(loss, dth):
+        seq_l += float(a)
+        seq_t += float(b)
+    assert (tot, tth) == (seq_l, seq_t)

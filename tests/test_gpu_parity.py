@@ -175,7 +175,10 @@ def test_loss_grad_parity(c1, theta):
         assert loss[d] == pytest.approx(lo, rel=1e-5)
         assert rel_norm(dq[d], dqo) < 1e-4
         # dL/dtheta is a sum of terms of both signs; FP32 rounding is measured
-        # against the sum of their magnitudes
+        # against the sum of their magnitudes, sum|terms| / |dL/dtheta| times
+        # larger than dL/dtheta itself (3 to 533 on these days)
+        print(f"day {d} theta {theta}: sum|terms| / |dtheta| = {dabs / abs(dtho):.1f}, "
+              f"relative dtheta error {abs(dth[d] - dtho) / abs(dtho):.2e}")
         assert abs(dth[d] - dtho) <= 1e-5 * dabs, (dth[d], dtho, dabs)
 
 

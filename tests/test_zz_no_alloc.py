@@ -2,10 +2,17 @@
 allocate device memory once running (a real-time loop that forbids
 allocation after start-up, memory owned by another allocator, or a path that
 cannot afford cudaMalloc's implicit synchronisation).  Its scratch is a
-file-scope device array shared by every call; the test checks it against
+file-scope device array shared by every call.  The tests check it against
 dode_loss, the allocating entry point, on two calls in a row (the second
-reusing what the first left in the array), and that oversized inputs are
+reusing what the first left in the array); on enough days that the array holds
+fewer resident CTAs than there are days; that a call on a fresh context
+changes the device's free memory by nothing; and that oversized inputs are
 refused with a clear error.  This file is collected last on purpose."""
+import os
+import subprocess
+import sys
+import textwrap
+
 import numpy as np
 import pytest
 
@@ -15,6 +22,8 @@ from tests.helpers import inputs
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,6 +48,72 @@ def test_static_scratch_loss_matches_dode_loss_twice(precision):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=1e-6, err_msg=f"call {call}")
+
+
+@pytest.mark.parametrize("precision", [dode.PREC_FP32, dode.PREC_BF16])
+def test_static_scratch_with_fewer_ctas_than_days(precision):
+    # 40 corridor days fill most of the 32 MiB array with q and the route
+    # choice, so it holds the residual slots of fewer CTAs than days: the CTAs
+    # then drain the days from the work queue
+    D = 40
+    w = synth.corridor_3yr(n_days=D)
+    days = list(range(D))
+    sp = w.speeds(days)
+    rng = np.random.default_rng(5)
+    counts = rng.uniform(0.0, 50.0, (D, w.n_intervals, w.net.n_obs)).astype(np.float32)
+    ctx = dode.Context.from_workload(w, precision=precision)
+    ctx.set_days(counts, sp, w.mask(days))
+    q = (w.q_true(days) * np.float32(0.8)).astype(np.float32)
+    out = torch.full((D,), -1.0, dtype=torch.float64, device="cuda")
+    ctx.loss_static_scratch(torch.from_numpy(q).cuda(), out, 0.1)
+    torch.cuda.synchronize()
+    grid = ctx.last_grid()
+    assert 1 <= grid < D, grid
+    ref = ctx.loss(q, 0.1)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-6)
+
+
+_NO_ALLOC_SCRIPT = textwrap.dedent("""
+    import sys
+    sys.path.insert(0, {root!r})
+    import numpy as np
+    import torch
+    from paper_1901_09266_gb300 import dode, synth
+    torch.cuda.init()
+    w = synth.corridor_3yr(n_days=4)
+    days = list(range(4))
+    sp = w.speeds(days)
+    counts = np.random.default_rng(3).uniform(0, 40, (4, w.n_intervals, w.net.n_obs)).astype(np.float32)
+    q = torch.from_numpy(w.q_true(days)).cuda()
+    out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    # another context runs the same kernels first (with allocation), so the
+    # driver's per-launch resources are in place before the measurement
+    warm = dode.Context.from_workload(w, precision={prec})
+    warm.set_days(counts, sp, w.mask(days))
+    warm.loss(q.cpu().numpy(), 0.1)
+    # a fresh context: its days are loaded, nothing else has run on it
+    ctx = dode.Context.from_workload(w, precision={prec})
+    ctx.set_days(counts, sp, w.mask(days))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ctx.loss_static_scratch(q, out, 0.1)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    ref = ctx.loss(q.cpu().numpy(), 0.1)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-6)
+    print("free", free0, free1)
+    assert free0 == free1, (free0, free1)
+""")
+
+
+@pytest.mark.parametrize("precision", [dode.PREC_FP32, dode.PREC_BF16])
+def test_static_scratch_allocates_nothing(precision):
+    # a clean process with every CUDA module loaded at start-up, so that the
+    # array itself is not allocated by a lazy module load inside the call
+    env = dict(os.environ, CUDA_MODULE_LOADING="EAGER")
+    r = subprocess.run([sys.executable, "-c", _NO_ALLOC_SCRIPT.format(root=ROOT, prec=precision)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
 
 
 def test_static_scratch_rejects_oversized_input():
