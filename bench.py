@@ -9,9 +9,12 @@ day-iteration = one full-row Adagrad update of one day), whole job.
 
 Default workload: the 3-year corridor (1096 days x 288 five-minute intervals,
 150 OD pairs, 300 routes, 400 detectors, 10 % missing), 500 epochs per step,
-fused form with BF16 operands.  Inputs (~1.3 GB) exceed the 129 MB L2, and
-every step reloads them.  The plain FP32 form and the fused FP32 form are timed
-beside it at --compare-epochs epochs.
+fused form in FP32 (the paper's precision).  Inputs (~1.3 GB) exceed the
+129 MB L2, and every step reloads them.  Beside it, untimed by the step clock:
+the plain FP32, fused FP32 and fused BF16 forms at --compare-epochs epochs; the
+uneven-day workload over 1 .. 1096 days per launch (autotuned, direct and
+graph); the next rows; and the loss-and-gradient form on all 1096 days of the
+600-OD corridor in both precisions.
 
 Under torchrun (N > 1) each rank solves its own 1096 days (weak scaling, days
 d + 1096 * rank of the same generator); ranks exchange only the timing.
@@ -48,27 +51,33 @@ def shard_days(n_days: int, rank: int, world: int) -> list:
     return list(range(rank * n_days, (rank + 1) * n_days))
 
 
-def measured_traffic(workload: str, precision: str, key: str = "bytes_per_day_iteration"):
-    """Per day-iteration figure ``key`` (DRAM bytes, or warp instructions) of the
-    fused kernel from the committed ncu summary, if it was taken of this
-    workload, this precision and the current kernel source (matched by hash);
-    else None."""
+def measured_traffic(form: str, workload: str, precision: str, key: str = "bytes_per_day_iteration"):
+    """Per day-iteration figure ``key`` (DRAM bytes, or warp instructions) of one
+    form of the solve, from the committed ncu summaries (profiles/*_traffic.txt),
+    if one was taken of this form, workload and precision and of the kernel
+    source as it is now (matched by hash); else None."""
+    import glob
     import hashlib
-    path = os.path.join(ROOT, "profiles", "fused_kernel_corridor-3yr-152d_traffic.txt")
-    try:
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*_traffic.txt"))):
         rec = {}
-        for line in open(path):
-            if "=" in line and not line.startswith("#"):
-                k, v = line.split("=", 1)
-                rec[k.strip()] = v.strip()
-        src = open(os.path.join(ROOT, "paper_1901_09266_gb300", "csrc", "fused.cu"), "rb").read()
-    except OSError:
-        return None
-    if hashlib.sha256(src).hexdigest()[:16] != rec.get("fused_cu_sha256_16"):
-        return None
-    if workload != "corridor-3yr" or precision != "bf16" or "BF16" not in rec.get("kernel", ""):
-        return None
-    return float(rec[key]) if key in rec else None
+        try:
+            for line in open(path):
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    rec[k.strip()] = v.strip()
+        except OSError:
+            continue
+        if (rec.get("form"), rec.get("workload"), rec.get("precision")) != (form, workload, precision):
+            continue
+        try:
+            src = open(os.path.join(ROOT, rec.get("source", "")), "rb").read()
+        except OSError:
+            continue
+        if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
+            continue
+        if key in rec:
+            return float(rec[key])
+    return None
 
 
 def _peaks() -> dict:
@@ -363,17 +372,18 @@ def run_gpu(args):
 
     # roofline of the fused kernel (algorithmic bytes / CUDA-event duration)
     peaks = _peaks()
+    peak = peaks.get("hbm_gbs")
     per_unit = algorithmic_bytes(N, O, A, K)
     kms = float(np.mean(kern_ms))
     achieved = per_unit * D * E / (kms / 1e3) / 1e9
-    peak = peaks.get("hbm_gbs")
+    form_name = "plain" if form == dode.FORM_PLAIN else "fused"
     traffic, traffic_src = args.traffic, "command line" if args.traffic is not None else None
-    if traffic is None and form == dode.FORM_FUSED:
-        per = measured_traffic(w.name, args.precision)
+    if traffic is None:
+        per = measured_traffic(form_name, w.name, args.precision)
         if per is not None:
             traffic = per * D * E
-            traffic_src = ("ncu dram__bytes_read+write of a 152-day, 2-epoch capture of this kernel, "
-                           "scaled by day-iterations (profiles/fused_kernel_corridor-3yr-152d_traffic.txt)")
+            traffic_src = (f"ncu dram__bytes_read+write of a 152-day capture of this {form_name} {args.precision} "
+                           "kernel source, scaled by day-iterations (profiles/*_traffic.txt)")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak if peak else 6800.0, "unit": "GB/s",
             "frac": achieved / (peak if peak else 6800.0), "traffic": traffic, "traffic_source": traffic_src,
             "peak_source": "measured" if peak else "fallback", "bytes_per_unit": per_unit,
@@ -382,24 +392,28 @@ def run_gpu(args):
     # instruction-issue roofline: measured warp instructions per day-iteration x
     # day-iterations/s of the kernel against 4 issue slots per SM per cycle at the
     # sampled clock
-    issue = None
-    ipu = measured_traffic(w.name, args.precision, "warp_instructions_per_day_iteration") \
-        if form == dode.FORM_FUSED else None
-    if ipu is not None:
-        mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
-        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak_issue = n_sm * 4 * mhz * 1e6
-        got = ipu * D * E / (kms / 1e3)
-        issue = {"bound": "issue", "achieved": got, "peak": peak_issue, "unit": "warp-instr/s",
-                 "frac": got / peak_issue, "instr_per_unit": ipu,
-                 "source": "ncu smsp__inst_executed.sum of a 152-day capture of this kernel"}
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
 
-    # comparison forms at equal epochs from q = 0: plain FP32, fused FP32, and this form
+    def issue_roof(form_key, precision, di_per_s):
+        ipu = measured_traffic(form_key, w.name, precision, "warp_instructions_per_day_iteration")
+        if ipu is None:
+            return None
+        peak_issue = n_sm * 4 * mhz * 1e6
+        return {"bound": "issue", "achieved": ipu * di_per_s, "peak": peak_issue, "unit": "warp-instr/s",
+                "frac": ipu * di_per_s / peak_issue, "instr_per_unit": ipu,
+                "source": "ncu smsp__inst_executed.sum of a 152-day capture of this kernel source"}
+
+    issue = issue_roof(form_name, args.precision, D * E / (kms / 1e3))
+
+    # comparison forms at equal epochs from q = 0: plain FP32, fused FP32 and
+    # fused BF16, each with its measured DRAM bytes per day-iteration (ncu
+    # summary of the same kernel source) and the DRAM rate they imply
     forms = {}
     if args.compare_epochs > 0 and rank == 0:
-        for name, fm, pr in [("plain_fp32", dode.FORM_PLAIN, dode.PREC_FP32),
-                             ("fused_fp32", dode.FORM_FUSED, dode.PREC_FP32),
-                             ("fused_bf16", dode.FORM_FUSED, dode.PREC_BF16)]:
+        for name, fm, pr, fk, pk in [("plain_fp32", dode.FORM_PLAIN, dode.PREC_FP32, "plain", "fp32"),
+                                     ("fused_fp32", dode.FORM_FUSED, dode.PREC_FP32, "fused", "fp32"),
+                                     ("fused_bf16", dode.FORM_FUSED, dode.PREC_BF16, "fused", "bf16")]:
             c2 = dode.Context.from_workload(w, form=fm, precision=pr)
             c2.use_torch_stream()
             c2.set_days(ct_d, sp_d, mk_d)
@@ -414,14 +428,73 @@ def run_gpu(args):
             b.record()
             torch.cuda.synchronize()
             t = a.elapsed_time(b) / 1e3
-            forms[name] = {"day_iter_per_s": D * args.compare_epochs / t,
-                           "final_loss": float(l_d.double().sum().item()), "kernel_ms": c2.last_kernel_ms(),
-                           "launches": c2.last_launches()}
+            rate = D * args.compare_epochs / t
+            mb = measured_traffic(fk, w.name, pk)
+            pk_gbs = peak if peak else 6800.0
+            forms[name] = {"day_iter_per_s": rate, "final_loss": float(l_d.double().sum().item()),
+                           "kernel_ms": c2.last_kernel_ms(), "launches": c2.last_launches(),
+                           "roofline": {"bound": "hbm", "achieved": per_unit * rate / 1e9, "peak": pk_gbs,
+                                        "unit": "GB/s", "frac": per_unit * rate / 1e9 / pk_gbs,
+                                        "bytes_per_unit": per_unit},
+                           "measured_bytes_per_day_iter": mb,
+                           "measured_dram_gbs": (mb * rate / 1e9) if mb is not None else None,
+                           "issue_roofline": issue_roof(fk, pk, rate)}
             c2.close()
         base = forms["plain_fp32"]
         for v in forms.values():
             v["speedup_vs_plain_fp32"] = v["day_iter_per_s"] / base["day_iter_per_s"]
             v["final_loss_rel_diff_vs_plain"] = abs(v["final_loss"] - base["final_loss"]) / base["final_loss"]
+        f32, f16 = forms["fused_fp32"], forms["fused_bf16"]
+        forms["bf16_vs_fp32"] = {
+            "day_iter_per_s_ratio": f16["day_iter_per_s"] / f32["day_iter_per_s"],
+            "measured_bytes_ratio": (f16["measured_bytes_per_day_iter"] / f32["measured_bytes_per_day_iter"]
+                                     if f16["measured_bytes_per_day_iter"] and f32["measured_bytes_per_day_iter"]
+                                     else None),
+            "final_loss_rel_diff": abs(f16["final_loss"] - f32["final_loss"]) / f32["final_loss"]}
+
+    # BASELINE config 3: uneven days (per-day observed subsets, missing rates
+    # U(0, 30 %)) in one persistent launch, the launch shape picked by the
+    # autotuner, direct launches against CUDA-graph replay, for days per launch
+    # swept over 1 .. 1096
+    config3 = None
+    if args.uneven_sweep and rank == 0:
+        from paper_1901_09266_gb300 import autotune
+        wu = make_workload("corridor-uneven", max(args.uneven_days))
+        du = list(range(max(args.uneven_days)))
+        spu, ctu, mku = gpu_inputs(wu, du)
+        spu_d, ctu_d, mku_d = (torch.from_numpy(a).to(dev) for a in (spu, ctu, mku))
+        points = []
+        for n in args.uneven_days:
+            pt_ = {"days": n}
+            qn = torch.empty((n, N, K), dtype=torch.float32, device=dev)
+            ln = torch.empty(n, dtype=torch.float64, device=dev)
+            for graph in (0, 1):
+                cu = dode.Context.from_workload(wu, precision=prec, use_graph=graph)
+                cu.use_torch_stream()
+                cu.set_days(ctu_d[:n], spu_d[:n], mku_d[:n])
+                tuned_u = autotune.tune(cu, iters=3, step=args.step, n_sm=n_sm, cache_path=None)
+                cu.set_days(ctu_d[:n], spu_d[:n], mku_d[:n])
+                cu.solve(args.uneven_epochs, args.step, args.batch, q_out=qn, loss_out=ln)     # warm-up / capture
+                cu.set_days(ctu_d[:n], spu_d[:n], mku_d[:n])
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                cu.solve(args.uneven_epochs, args.step, args.batch, q_out=qn, loss_out=ln)
+                b.record()
+                torch.cuda.synchronize()
+                t = a.elapsed_time(b) / 1e3
+                pt_["graph" if graph else "direct"] = {
+                    "day_iter_per_s": n * args.uneven_epochs / t, "call_ms": t * 1e3,
+                    "kernel_ms": cu.last_kernel_ms(), "grid": cu.last_grid(),
+                    "shape": {k: tuned_u[k] for k in ("block", "ctas_per_sm", "max_ctas")},
+                    "final_loss": float(ln.double().sum().item())}
+                cu.close()
+            points.append(pt_)
+        config3 = {"workload": wu.name, "epochs": args.uneven_epochs, "precision": args.precision,
+                   "observed_links_per_day": [int(x) for x in (mku.reshape(len(du), N, O).any(axis=1).sum(axis=1)
+                                                               [[0, -1]])],
+                   "points": points}
+        del spu_d, ctu_d, mku_d
 
     # next rows on the same days: pattern-level route choice (weekday / weekend /
     # holiday labels), the R^2 quality check and the DAR distance to the mean DAR
@@ -487,28 +560,47 @@ def run_gpu(args):
         del Bd, Yd
 
     # form 3 (differentiable) on the 600-OD / 1500-route / 1000-detector corridor:
-    # loss and gradients (dL/dq, dL/dtheta) of every day, DAR recomputed in both passes
+    # loss and gradients (dL/dq, dL/dtheta) of every day, DAR recomputed in both
+    # passes, in FP32 and BF16
     form3 = None
     if args.form3_days > 0 and rank == 0:
         w5 = make_workload("corridor-large", args.form3_days)
         d5 = list(range(args.form3_days))
         sp5, ct5, mk5 = gpu_inputs(w5, d5)
-        c5 = dode.Context.from_workload(w5, precision=prec)
-        c5.use_torch_stream()
-        c5.set_days(ct5, sp5, mk5)
+        sp5_d, ct5_d, mk5_d = (torch.from_numpy(a).to(dev) for a in (sp5, ct5, mk5))
         q5 = torch.from_numpy(w5.q_true(d5) * np.float32(0.9)).to(dev)
         dq5 = torch.empty_like(q5)
-        c5.loss_grad(q5, 0.1, dq_out=dq5)                     # warm-up
-        ms5 = []
-        for _ in range(3):
-            loss5, _, dth5 = c5.loss_grad(q5, 0.1, dq_out=dq5)
-            ms5.append(c5.last_kernel_ms())
-        form3 = {"workload": w5.name, "days": len(d5), "routes": w5.routes.n_routes, "od_pairs": w5.routes.n_od,
-                 "detectors": w5.net.n_obs, "kernel_ms": min(ms5),
-                 "day_loss_grads_per_s": len(d5) / (min(ms5) / 1e3),
-                 "total_loss": float(np.sum(loss5)), "dtheta_total": float(np.sum(dth5))}
-        c5.close()
-        del q5, dq5
+        N5, O5, A5, K5 = w5.n_intervals, w5.net.n_obs, w5.net.n_links, w5.routes.n_od
+        # bytes one loss+gradient pass of a day must move: counts, mask bits,
+        # uint16 ticks, q read, dL/dq written, loss and dL/dtheta
+        per5 = 4 * N5 * O5 + (N5 * O5) // 8 + 2 * N5 * A5 + 4 * N5 * K5 + 4 * N5 * K5 + 16
+        form3 = {"workload": w5.name, "days": len(d5), "routes": w5.routes.n_routes, "od_pairs": K5,
+                 "detectors": O5, "bytes_per_day_pass": per5}
+        res5 = {}
+        for pname, pr in (("fp32", dode.PREC_FP32), ("bf16", dode.PREC_BF16)):
+            c5 = dode.Context.from_workload(w5, precision=pr)
+            c5.use_torch_stream()
+            c5.set_days(ct5_d, sp5_d, mk5_d)
+            c5.loss_grad(q5, 0.1, dq_out=dq5)                     # warm-up
+            ms5 = []
+            for _ in range(3):
+                loss5, _, dth5 = c5.loss_grad(q5, 0.1, dq_out=dq5)
+                ms5.append(c5.last_kernel_ms())
+            t5 = min(ms5) / 1e3
+            res5[pname] = (np.asarray(loss5, np.float64), dq5.detach().cpu().numpy().astype(np.float64),
+                           np.asarray(dth5, np.float64))
+            pk_gbs = peak if peak else 6800.0
+            form3[pname] = {"kernel_ms": t5 * 1e3, "day_loss_grads_per_s": len(d5) / t5,
+                            "roofline": {"bound": "hbm", "achieved": per5 * len(d5) / t5 / 1e9, "peak": pk_gbs,
+                                         "unit": "GB/s", "frac": per5 * len(d5) / t5 / 1e9 / pk_gbs},
+                            "total_loss": float(np.sum(loss5)), "dtheta_total": float(np.sum(dth5))}
+            c5.close()
+        (l32, g32, t32), (l16, g16, t16) = res5["fp32"], res5["bf16"]
+        form3["bf16_vs_fp32"] = {
+            "loss_max_rel": float(np.max(np.abs(l16 - l32) / np.abs(l32))),
+            "dq_max_rel_norm": float(np.max(np.sqrt(((g16 - g32) ** 2).sum(axis=(1, 2)) / (g32 ** 2).sum(axis=(1, 2))))),
+            "dtheta_max_rel": float(np.max(np.abs(t16 - t32) / np.abs(t32)))}
+        del q5, dq5, sp5_d, ct5_d, mk5_d
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -539,6 +631,7 @@ def run_gpu(args):
             "clocks": clk,
             "forms": forms,
             "next": nxt,
+            "config3": config3,
             "form3": form3,
             "final_loss_total": final_loss,
         }
@@ -565,15 +658,20 @@ def main(argv=None):
     ap.add_argument("--row-chunk", type=int, default=0,
                     help="Algorithm 1's row batch b (0 = all observed rows in each update)")
     ap.add_argument("--form", default="fused", choices=["fused", "plain"])
-    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--ctas", type=int, default=0)
     ap.add_argument("--graph", action="store_true", help="replay the solve as a CUDA graph")
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with the autotuner")
     ap.add_argument("--compare-epochs", type=int, default=20)
     ap.add_argument("--next-rows", type=int, default=1, help="time the pattern, R^2, DAR-distance and dense rows")
-    ap.add_argument("--form3-days", type=int, default=152,
+    ap.add_argument("--form3-days", type=int, default=1096,
                     help="days of the corridor-large loss+gradient timing (0 = skip)")
+    ap.add_argument("--uneven-sweep", type=int, default=1,
+                    help="time the uneven-day workload over --uneven-days days per launch (0 = skip)")
+    ap.add_argument("--uneven-days", type=lambda v: [int(x) for x in v.split(",")],
+                    default=[1, 2, 8, 64, 256, 1096])
+    ap.add_argument("--uneven-epochs", type=int, default=50)
     ap.add_argument("--dense-n", type=int, default=6000)
     ap.add_argument("--dense-iters", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -243,19 +243,35 @@ int dode_last_totals(dode_ctx *ctx, double *loss_total, double *dtheta_total);
  *   loss       [m] FP64 out: ||B x_j - y_j||^2 of the final iterate
  *   method     0 = automatic, 1 = one pass over B per iteration (rows of B are
  *              streamed into shared memory by bulk asynchronous copies and used
- *              for both products; needs m = 1, n_cols % 4 == 0, n_cols <= 8192 and
- *              a 16-byte aligned B, else DODE_ERR_UNSUPPORTED), 2 = two passes
- *              (one per product).  Automatic takes one pass when it applies.
+ *              for both products; all iterations run in one cooperative launch
+ *              with a grid-wide step between passes; needs m = 1,
+ *              n_cols % 4 == 0, n_cols <= 8192, a 16-byte aligned B and a device
+ *              that supports cooperative launches, else DODE_ERR_UNSUPPORTED),
+ *              2 = two passes (one per product).  Automatic takes one pass when
+ *              it applies.
  *   kernel_ms  out (may be NULL): GPU time of the iterations and the final residual
  * All arrays are host or device pointers per ptr_kind; stream is a cudaStream_t
  * (NULL = default stream); the call returns when its work is complete.
  * Limits: 1 <= m <= 8 and n_cols * m <= 51200 (x is staged in shared memory).
  * Errors: DODE_ERR_ARG, DODE_ERR_UNSUPPORTED (the limits), DODE_ERR_OOM, DODE_ERR_CUDA,
- * DODE_ERR_DEVICE_TIMEOUT (a bounded wait for a bulk copy expired); the message goes to stderr.
+ * DODE_ERR_DEVICE_TIMEOUT (a bounded device wait of the one-pass kernel ran out: a
+ * row copy, or the grid-wide step); the message goes to stderr.  After a timeout
+ * the library stays usable: the kernel lets its copies in flight land before it
+ * returns.
  */
 int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, const float *Y, int32_t iters,
                     float step, float eps, int32_t method, float *X, float *G, double *loss, double *kernel_ms,
                     int32_t ptr_kind, void *stream);
+
+/*
+ * dode_dense_set_wait_limit -- how many times a bounded wait of the one-pass
+ * dense kernel (method 1) polls for a row copy before it gives up with
+ * DODE_ERR_DEVICE_TIMEOUT (default 2^26; process-wide).  0 makes every such
+ * wait give up at once, which exercises the failure path without a fault; the
+ * kernel's final wait for its own copies in flight keeps its fixed limit.
+ * Errors: DODE_ERR_ARG (polls < 0).
+ */
+int dode_dense_set_wait_limit(int64_t polls);
 
 /*
  * dode_set_patterns -- traffic patterns of the loaded days (Step 2-3 of the

@@ -277,6 +277,7 @@ static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 size_t fused_smem_bytes(const dode_ctx *ctx, int R, int RW) {
     size_t off = align16((size_t)ctx->P * 16) + align16((size_t)(ctx->G + 1) * 4) + align16((size_t)ctx->G * 4) +
+                 align16((ctx->god_ptr.size() + ctx->god.size() + ctx->godr_ptr.size() + ctx->godr.size()) * 4) +
                  align16((size_t)ctx->Ow * 4);
     if (R > 0) off = align16(off + (size_t)ctx->O * R * 4);
     if (RW > 0) off += (size_t)ctx->A * RW * 2;
@@ -558,6 +559,8 @@ FusedParams base_params(dode_ctx *ctx) {
     p.god = ctx->d_god;
     p.godr_ptr = ctx->d_godr_ptr;
     p.godr = ctx->d_godr;
+    p.n_god = (int)ctx->god.size();
+    p.n_godr = (int)ctx->godr.size();
     p.step_ods = ctx->d_step_ods;
     p.n_step_ods = (int)ctx->step_ods.size();
     p.pt = ctx->d_pt;
@@ -1425,6 +1428,15 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
     return DODE_OK;
 }
 
+// Polls of a bounded wait in the one-pass dense kernel before it gives up.
+static long long g_dense_wait_limit = 1ll << 26;
+
+int dode_dense_set_wait_limit(int64_t polls) {
+    if (polls < 0) return DODE_ERR_ARG;
+    g_dense_wait_limit = polls;
+    return DODE_OK;
+}
+
 int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, const float *Y, int32_t iters,
                     float step, float eps, int32_t method, float *X, float *G, double *loss, double *kernel_ms,
                     int32_t ptr_kind, void *stream) {
@@ -1458,12 +1470,16 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t xbytes = ((size_t)n_cols * 4 + 127) & ~(size_t)127;
-    const size_t room = (size_t)optin > xbytes + 1024 ? (size_t)optin - xbytes - 1024 : 0;
-    const int RB = (int)std::min<size_t>(8, room / ((size_t)2 * n_cols * 4));
-    const bool one_ok = m == 1 && n_cols % 4 == 0 && n_cols <= 8192 && RB >= 1 &&
+    const size_t room = (size_t)optin > xbytes + 2048 ? (size_t)optin - xbytes - 2048 : 0;
+    // ring stages of one row: 8 or 4 (a multiple of the kernel's four residual warps)
+    const int S = (int)(std::min<size_t>(8, room / ((size_t)n_cols * 4)) & ~(size_t)3);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const bool one_ok = m == 1 && n_cols % 4 == 0 && n_cols <= 8192 && S >= 4 && coop &&
                         (host || ((uintptr_t)B % 16 == 0));
     if (method == 1 && !one_ok)
-        return bail(DODE_ERR_UNSUPPORTED, "one pass needs m = 1, n_cols % 4 == 0, n_cols <= 8192, 16-byte aligned B");
+        return bail(DODE_ERR_UNSUPPORTED,
+                    "one pass needs m = 1, n_cols % 4 == 0, n_cols <= 8192, 16-byte aligned B, cooperative launch");
     const bool one = method == 1 || (method == 0 && one_ok);
     const int grid_f = n_sm;
     // one device allocation: (B, y when on the host) x, G, r, gradient partials, loss
@@ -1479,7 +1495,7 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     const size_t oX = take(nX), oG = take(nX), oR = take(nY);
     const size_t oP = take((size_t)std::max(p.grid_g, grid_f) * nX);
     const size_t n_lpart = (size_t)std::max(p.grid_r, grid_f) * m;
-    const size_t d_count = n_lpart + m + 1;
+    const size_t d_count = n_lpart + m + 2;
     char *buf = nullptr;
     const size_t f_bytes = off * sizeof(float);
     if (cudaMalloc(&buf, f_bytes + d_count * sizeof(double)) != cudaSuccess) {
@@ -1497,7 +1513,9 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     p.lpart = reinterpret_cast<double *>(buf + f_bytes);
     double *dloss = p.lpart + n_lpart;
     int *derr = reinterpret_cast<int *>(dloss + m);
-    const size_t fsmem = xbytes + (size_t)2 * RB * n_cols * 4;
+    unsigned int *dgbar = reinterpret_cast<unsigned int *>(dloss + m + 1);
+    p.wait_limit = g_dense_wait_limit;
+    const size_t fsmem = xbytes + (size_t)S * n_cols * 4;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     cudaError_t e = cudaSuccess;
@@ -1507,15 +1525,22 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
     if (e == cudaSuccess)
         e = G ? cudaMemcpyAsync(p.G, G, nX * sizeof(float), in, st) : cudaMemsetAsync(p.G, 0, nX * sizeof(float), st);
     if (e == cudaSuccess) e = dense_set_smem((size_t)n_cols * m * sizeof(float), (size_t)p.rows_per_cta * m * sizeof(float));
-    if (e == cudaSuccess && one) e = dense_fused_set_smem(fsmem);
+    if (e == cudaSuccess && one) e = dense_persist_set_smem(fsmem);
     if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    for (int it = 0; it < iters && e == cudaSuccess; ++it)
-        e = one ? dense_fused_iteration(p, grid_f, RB, fsmem, derr, st) : dense_iteration(p, true, st);
-    if (e == cudaSuccess) e = dense_iteration(p, false, st);     // residual and loss of the final x
-    if (e == cudaSuccess) e = dense_loss(p, dloss, st);
+    if (one) {
+        // every iteration and the final residual pass in one launch; loss partials per CTA
+        if (e == cudaSuccess) e = dense_persist(p, iters, grid_f, S, fsmem, derr, dgbar, st);
+        DenseParams pl = p;
+        pl.grid_r = grid_f;
+        if (e == cudaSuccess) e = dense_loss(pl, dloss, st);
+    } else {
+        for (int it = 0; it < iters && e == cudaSuccess; ++it) e = dense_iteration(p, true, st);
+        if (e == cudaSuccess) e = dense_iteration(p, false, st);     // residual and loss of the final x
+        if (e == cudaSuccess) e = dense_loss(p, dloss, st);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
     const cudaMemcpyKind out = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (e == cudaSuccess) e = cudaMemcpyAsync(X, p.x, nX * sizeof(float), out, st);
@@ -1536,7 +1561,7 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
         (void)cudaGetLastError();
         return bail(DODE_ERR_CUDA, cudaGetErrorString(e));
     }
-    if (herr) return bail(DODE_ERR_DEVICE_TIMEOUT, "a bulk copy of B did not complete in time");
+    if (herr) return bail(DODE_ERR_DEVICE_TIMEOUT, "a bounded wait of the one-pass kernel ran out");
     return DODE_OK;
 }
 

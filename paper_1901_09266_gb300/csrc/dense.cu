@@ -171,156 +171,291 @@ __global__ void k_dense_loss(const double *__restrict__ lpart, int n_part, int m
 }
 
 // ---------------------------------------------------------------------------
-// One pass over B per iteration (one right-hand side, n_cols % 4 == 0 and
-// n_cols <= 8192): a persistent CTA per SM streams blocks of RB rows of B into
-// shared memory with bulk asynchronous copies (TMA, two stages completed on
-// mbarriers), forms the block's residuals r = B x - y from shared memory, and
-// adds r B to a partial gradient held in registers (each thread owns 4-column
-// strips c = 4 tid + 1024 k).  Partials go to gpart[cta], reduced by
-// k_dense_step.  Every mbarrier wait is bounded: on expiry the kernel records
-// an error, waits (bounded) for its copies in flight and returns.
+// One pass over B per iteration, every iteration in one cooperative launch
+// (one right-hand side, n_cols % 4 == 0, n_cols <= 8192, 16-byte aligned B).
+// CTA c (one per SM, all resident) owns rows [c rpc, (c + 1) rpc) of B and
+// streams them, row by row, through a ring of S shared-memory stages with bulk
+// asynchronous copies (TMA).  B does not change between iterations, so the
+// copies run on into the next iteration's rows while the grid synchronises.
+// Warp roles, synchronised by mbarriers only:
+//   warp 8      producer: one lane issues row copies into free stages
+//               (full[s] completes when the row has landed; empty[s] when the
+//               consumers are done with the stage)
+//   warps 0..3  residuals: warp w takes the row copies q = w mod 4 (counted
+//               over the whole launch) and forms r_j = B_j . x - y_j from shared
+//               memory (a warp sum), publishing it through rready[s]
+//   warps 4..7  gradient: thread t owns the 4-column strips c = 4 t + 512 k and
+//               adds r_j B_j to them, rows in order
+// After its rows the CTA writes its partial gradient to gpart[cta]; grid
+// barrier; CTA c sums the partials of its columns in a fixed order and takes
+// Algorithm 1's step for them (Adagrad and projection); grid barrier; every CTA
+// reloads x.  Pass `iters` forms the residuals and the loss of the final x only.
+// Every wait is bounded (wait_limit polls for the stream, a fixed limit for the
+// drain and the grid barriers); a wait that runs out sets the error word, the
+// producer stops issuing and lets its copies in flight land (bounded), the grid
+// barriers give up once the error word is set, and the kernel returns.
 // ---------------------------------------------------------------------------
-constexpr int kFusedStrips = 8;                      // n_cols <= 8 * 1024
+constexpr int kPersistStages = 8;                   // ring stages (rows): 4 or 8, a multiple of the residual warps
+constexpr int kPersistStrips = 16;                  // n_cols <= 16 * 512
+constexpr int kPersistThreads = 288;                // 8 compute warps + 1 producer warp
+constexpr long long kDrainLimit = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < (1ll << 26); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of `bar` with this parity: at most `limit` polls, and none
+// once *abort is set.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit, const volatile int *abort) {
+    for (long long it = 0; it < limit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (abort && *abort) return false;
     }
     return false;
 }
 
-// Thread 0: expect `bytes` on bar, then copy rows [r0, r0 + n) of B into dst.
-__device__ __forceinline__ void issue_rows(const float *B, int nc, int r0, int n, float *dst, uint64_t *bar) {
-    const uint32_t bytes = (uint32_t)n * (uint32_t)nc * 4u;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-    for (int i = 0; i < n; ++i)
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(dst + (size_t)i * nc)),
-            "l"(B + (size_t)(r0 + i) * nc), "r"((uint32_t)nc * 4u), "r"(smem_u32(bar))
-            : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__global__ void __launch_bounds__(256, 1) k_dense_fused(const DenseParams p, int RB, int *err) {
+// Grid barrier number k of the launch (all CTAs resident: cooperative launch):
+// one thread per CTA arrives on the counter and polls it, at most `limit`
+// polls, giving up once the error word is set.
+__device__ bool grid_barrier(unsigned int *count, unsigned int k, const volatile int *err, long long limit) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    const unsigned int target = gridDim.x * (k + 1);
+    for (long long it = 0; it < limit; ++it) {
+        unsigned int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+        if (v >= target) return true;
+        if (*err) return false;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    k_dense_persist(const DenseParams p, int iters, int S, int *err, unsigned int *gbar) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ float rblk[8];
-    __shared__ double lred[8];
+    __shared__ __align__(8) uint64_t full[kPersistStages], empty[kPersistStages], rready[kPersistStages];
+    __shared__ float rval[kPersistStages];
+    __shared__ float gred[8][32];
+    __shared__ double lred[4];
+    __shared__ int abort_cta;    // set by any warp whose wait ran out (the producer stops issuing)
+    __shared__ int stop_cta;     // the compute warps' common decision to stop, taken by thread 0 between barriers
     const int nc = p.nc, nr = p.nr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float *xs = reinterpret_cast<float *>(smem_raw);
     const size_t xbytes = ((size_t)nc * 4 + 127) & ~(size_t)127;
-    float *buf[2] = {reinterpret_cast<float *>(smem_raw + xbytes),
-                     reinterpret_cast<float *>(smem_raw + xbytes + (size_t)RB * nc * 4)};
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < nc; i += blockDim.x) xs[i] = p.x[i];
+    float *ring = reinterpret_cast<float *>(smem_raw + xbytes);
+    const int rpc = (nr + gridDim.x - 1) / gridDim.x;
+    const int row0 = blockIdx.x * rpc;
+    const int nrow = max(0, min(rpc, nr - row0));
+    const long long nseq = (long long)(iters + 1) * nrow;
+
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar[1])) : "memory");
+        for (int st = 0; st < S; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&rready[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 5;" ::"r"(smem_u32(&empty[st])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_cta = 0;
+        stop_cta = 0;
     }
+    for (int i = tid; i < nc; i += blockDim.x) xs[i] = __ldcg(p.x + i);
     __syncthreads();
-    const int nblk = (nr + RB - 1) / RB;
-    float acc[kFusedStrips][4];
-#pragma unroll
-    for (int k = 0; k < kFusedStrips; ++k)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[k][u] = 0.f;
-    double l2 = 0.0;
-    int blk = blockIdx.x, it = 0;
-    if (tid == 0 && blk < nblk) issue_rows(p.B, nc, blk * RB, min(RB, nr - blk * RB), buf[0], &bar[0]);
-    bool ok = true;
-    for (; blk < nblk; blk += gridDim.x, ++it) {
-        const int st = it & 1;
-        const int nxt = blk + gridDim.x;
-        if (tid == 0 && nxt < nblk) issue_rows(p.B, nc, nxt * RB, min(RB, nr - nxt * RB), buf[st ^ 1], &bar[st ^ 1]);
-        const bool landed = mbar_wait(&bar[st], (uint32_t)((it >> 1) & 1));
-        if (!__syncthreads_and(landed)) {                 // the same decision in every thread
-            ok = false;
-            break;
-        }
-        const int r0 = blk * RB, nrow = min(RB, nr - r0);
-        const float *rows = buf[st];
-        // residuals of the block: warp w takes row w
-        if (warp < nrow) {
-            const float *row = rows + (size_t)warp * nc;
-            float v = 0.f;
-            for (int c = 4 * lane; c < nc; c += 128) {
-                const float4 b = *reinterpret_cast<const float4 *>(row + c);
-                const float4 xv = *reinterpret_cast<const float4 *>(xs + c);
-                v += b.x * xv.x + b.y * xv.y + b.z * xv.z + b.w * xv.w;
-            }
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            const float ri = v - p.y[r0 + warp];
-            if (lane == 0) {
-                rblk[warp] = ri;
-                p.r[r0 + warp] = ri;
-            }
-            l2 += (double)ri * (double)ri;
-        }
-        __syncthreads();
-        // g += r B over the block's rows
-#pragma unroll
-        for (int k = 0; k < kFusedStrips; ++k) {
-            const int c = 4 * tid + 1024 * k;
-            if (c < nc)
-                for (int i = 0; i < nrow; ++i) {
-                    const float4 b = *reinterpret_cast<const float4 *>(rows + (size_t)i * nc + c);
-                    const float rv = rblk[i];
-                    acc[k][0] += b.x * rv;
-                    acc[k][1] += b.y * rv;
-                    acc[k][2] += b.z * rv;
-                    acc[k][3] += b.w * rv;
+
+    if (warp == 8) {
+        // ------------------------------ producer ------------------------------
+        if (lane == 0) {
+            long long issued = 0;
+            for (long long q = 0; q < nseq; ++q) {
+                const int st = (int)(q % S);
+                if (q >= S && !mbar_wait(&empty[st], (uint32_t)((q / S - 1) & 1), p.wait_limit, &abort_cta)) {
+                    abort_cta = 1;
+                    atomicCAS(err, 0, kErrDeviceTimeout);
+                    break;
                 }
+                if (abort_cta) break;
+                const uint32_t bytes = (uint32_t)nc * 4u;
+                float *dst = ring + (size_t)st * nc;
+                const float *src = p.B + (size_t)(row0 + (int)(q % nrow)) * nc;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
+                             "r"(bytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(dst)),
+                    "l"(src), "r"(bytes), "r"(smem_u32(&full[st]))
+                    : "memory");
+                issued = q + 1;
+            }
+            // the copies in flight write this CTA's shared memory: let them land
+            for (long long q = max(0ll, issued - S); q < issued; ++q)
+                mbar_wait(&full[q % S], (uint32_t)((q / S) & 1), kDrainLimit, nullptr);
         }
-        __syncthreads();                                  // stage st free for the copy after next
-    }
-    if (!ok) {
-        if (tid == 0) {
-            atomicCAS(err, 0, kErrDeviceTimeout);
-            // the copies in flight target this CTA's shared memory: let them land
-            const int st = it & 1;
-            mbar_wait(&bar[st], (uint32_t)((it >> 1) & 1));
-            if (blk + (int)gridDim.x < nblk) mbar_wait(&bar[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-        }
-        return;
-    }
-    float *gp = p.gpart + (size_t)blockIdx.x * nc;
+    } else {
+        // --------------------------- compute warps ----------------------------
+        const bool resid = warp < 4;
+        float acc[kPersistStrips][4];
+        unsigned int nbar = 0;
+        for (int it = 0; it <= iters; ++it) {
+            const bool last = it == iters;
 #pragma unroll
-    for (int k = 0; k < kFusedStrips; ++k) {
-        const int c = 4 * tid + 1024 * k;
-        if (c < nc) *reinterpret_cast<float4 *>(gp + c) = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+            for (int k = 0; k < kPersistStrips; ++k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[k][u] = 0.f;
+            double l2 = 0.0;
+            if (resid) {
+                // warp w takes the copies q = w mod 4 of the whole launch; with S a
+                // multiple of 4 the previous use of a stage (q - S) was this warp's
+                // too, so every wait is on the phase right after one it has seen
+                // complete (a parity wait cannot alias an older phase)
+                const long long qb = (long long)it * nrow, qe = qb + nrow;
+                for (long long q = qb + (((warp - qb) % 4) + 4) % 4; q < qe; q += 4) {
+                    const int j = (int)(q - qb);
+                    const int st = (int)(q % S);
+                    const bool ok = mbar_wait(&full[st], (uint32_t)((q / S) & 1), p.wait_limit, &abort_cta);
+                    float v = 0.f;
+                    if (ok) {
+                        const float *row = ring + (size_t)st * nc;
+                        for (int c = 4 * lane; c < nc; c += 128) {
+                            const float4 b = *reinterpret_cast<const float4 *>(row + c);
+                            const float4 xv = *reinterpret_cast<const float4 *>(xs + c);
+                            v += b.x * xv.x + b.y * xv.y + b.z * xv.z + b.w * xv.w;
+                        }
+                    } else if (lane == 0) {
+                        abort_cta = 1;
+                        atomicCAS(err, 0, kErrDeviceTimeout);
+                    }
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                    const float ri = v - __ldg(p.y + row0 + j);
+                    l2 += (double)ri * (double)ri;
+                    __syncwarp();
+                    if (lane == 0) {
+                        rval[st] = ri;
+                        mbar_arrive(&rready[st]);
+                        mbar_arrive(&empty[st]);
+                    }
+                }
+            } else {
+                const int t = tid - 128;
+                for (int j = 0; j < nrow; ++j) {
+                    const long long q = (long long)it * nrow + j;
+                    const int st = (int)(q % S);
+                    const uint32_t par = (uint32_t)((q / S) & 1);
+                    const bool ok = mbar_wait(&rready[st], par, p.wait_limit, &abort_cta) &&
+                                    mbar_wait(&full[st], par, p.wait_limit, &abort_cta);
+                    if (ok && !last) {
+                        const float rv = rval[st];
+                        const float *row = ring + (size_t)st * nc;
+#pragma unroll
+                        for (int k = 0; k < kPersistStrips; ++k) {
+                            const int c = 4 * t + 512 * k;
+                            if (c < nc) {
+                                const float4 b = *reinterpret_cast<const float4 *>(row + c);
+                                acc[k][0] += b.x * rv;
+                                acc[k][1] += b.y * rv;
+                                acc[k][2] += b.z * rv;
+                                acc[k][3] += b.w * rv;
+                            }
+                        }
+                    } else if (!ok && lane == 0) {
+                        abort_cta = 1;
+                        atomicCAS(err, 0, kErrDeviceTimeout);
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[st]);
+                }
+                if (!last) {
+                    float *gp = p.gpart + (size_t)blockIdx.x * nc;
+#pragma unroll
+                    for (int k = 0; k < kPersistStrips; ++k) {
+                        const int c = 4 * t + 512 * k;
+                        if (c < nc)
+                            *reinterpret_cast<float4 *>(gp + c) = make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+                    }
+                }
+            }
+            if (resid && lane == 0) lred[warp] = l2;
+            bar_compute();
+            if (last) {
+                if (tid == 0) p.lpart[blockIdx.x] = ((lred[0] + lred[1]) + lred[2]) + lred[3];
+                break;
+            }
+            // partial gradients of every CTA are written: sum them per column
+            if (tid == 0) {
+                if (!abort_cta && !grid_barrier(gbar, nbar, err, kDrainLimit)) {
+                    abort_cta = 1;
+                    atomicCAS(err, 0, kErrDeviceTimeout);
+                }
+                stop_cta = abort_cta;
+            }
+            ++nbar;
+            bar_compute();
+            if (stop_cta) break;
+            const int cpc = (nc + gridDim.x - 1) / gridDim.x;
+            const int c0 = blockIdx.x * cpc, c1 = min(nc, c0 + cpc);
+            for (int cb = c0; cb < c1; cb += 32) {
+                const int c = cb + lane;
+                float g = 0.f;
+                if (c < c1)
+                    for (int b = warp; b < (int)gridDim.x; b += 8) g += __ldcg(p.gpart + (size_t)b * nc + c);
+                gred[warp][lane] = g;
+                bar_compute();
+                if (warp == 0 && c < c1) {
+                    float gs = 0.f;
+                    for (int w = 0; w < 8; ++w) gs += gred[w][lane];
+                    const float Gv = __ldcg(p.G + c) + gs * gs;
+                    p.G[c] = Gv;
+                    p.x[c] = fmaxf(__ldcg(p.x + c) - p.eta * gs / (sqrtf(Gv) + p.eps), 0.f);
+                }
+                bar_compute();
+            }
+            // every CTA's columns are stepped: reload x
+            if (tid == 0) {
+                if (!abort_cta && !grid_barrier(gbar, nbar, err, kDrainLimit)) {
+                    abort_cta = 1;
+                    atomicCAS(err, 0, kErrDeviceTimeout);
+                }
+                stop_cta = abort_cta;
+            }
+            ++nbar;
+            bar_compute();
+            if (stop_cta) break;
+            for (int i = tid; i < nc; i += 256) xs[i] = __ldcg(p.x + i);
+            bar_compute();
+        }
     }
-    if (lane == 0) lred[warp] = l2;
     __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += lred[w];
-        p.lpart[blockIdx.x] = t;
-    }
 }
 
-cudaError_t dense_fused_iteration(const DenseParams &p, int grid, int RB, size_t smem, int *err, cudaStream_t s) {
-    k_dense_fused<<<grid, 256, smem, s>>>(p, RB, err);
-    cudaError_t e = cudaGetLastError();
+cudaError_t dense_persist(const DenseParams &p, int iters, int grid, int S, size_t smem, int *err, unsigned int *gbar,
+                          cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(gbar, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    k_dense_step<<<(p.nc + 31) / 32, 256, 0, s>>>(p.gpart, grid, p.nc, 1, p.eta, p.eps, p.x, p.G);
-    return cudaGetLastError();
+    DenseParams pp = p;
+    void *args[] = {&pp, &iters, &S, &err, &gbar};
+    return cudaLaunchCooperativeKernel((const void *)k_dense_persist, dim3(grid), dim3(kPersistThreads), args, smem, s);
 }
 
-cudaError_t dense_fused_set_smem(size_t bytes) {
-    return cudaFuncSetAttribute(k_dense_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t dense_persist_set_smem(size_t bytes) {
+    return cudaFuncSetAttribute(k_dense_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 cudaError_t dense_iteration(const DenseParams &p, bool step, cudaStream_t s) {

@@ -84,6 +84,7 @@ struct FusedParams {
     const int32_t *god;        // owned ODs
     const int32_t *godr_ptr;   // routes of each owned OD in godr
     const int32_t *godr;       // their indices in the group's walk order
+    int n_god, n_godr;         // sizes of god and godr
     const int32_t *step_ods;   // [n_step_ods] ODs whose routes span groups: step pass
     int n_step_ods;
     const float *pt;           // [D][P][Np] route choice for the call's theta
@@ -186,6 +187,7 @@ struct DenseParams {
     int nr, nc, m, grid_r, grid_g, rows_per_cta;
     int vec;                   // rows of B start on 16-byte boundaries (n_cols % 4 == 0, aligned base)
     float eta, eps;
+    long long wait_limit;      // polls of a bounded wait on a row copy before it gives up
 };
 
 // error codes mirrored from dode.h for device use
@@ -225,8 +227,9 @@ cudaError_t launch_dar_distance(const DarParams &p, double *part, int n_part, do
 cudaError_t dense_iteration(const DenseParams &p, bool step, cudaStream_t s);
 cudaError_t dense_loss(const DenseParams &p, double *loss, cudaStream_t s);
 cudaError_t dense_set_smem(size_t resid_bytes, size_t grad_bytes);
-cudaError_t dense_fused_iteration(const DenseParams &p, int grid, int RB, size_t smem, int *err, cudaStream_t s);
-cudaError_t dense_fused_set_smem(size_t bytes);
+cudaError_t dense_persist(const DenseParams &p, int iters, int grid, int S, size_t smem, int *err, unsigned int *gbar,
+                          cudaStream_t s);
+cudaError_t dense_persist_set_smem(size_t bytes);
 cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);

@@ -94,6 +94,10 @@ struct Shared {
     const int4 *groute;   // [P] walk order: (route, first position, links, start depth)
     const int *gptr;      // [G+1] routes of each walk group
     const int *task_grp;  // [G] processing order
+    const int *god_ptr;   // [G+1] ODs owned by each walk group (shared-memory copies of the
+    const int *god;       //        OD-update tables: read by every adjoint task, so they are
+    const int *godr_ptr;  //        kept out of the global load path)
+    const int *godr;
     const int2 *rtab;     // [L] route-position table in shared memory, or null
     const uint32_t *rtab32;  // [L] its 32-bit form in shared memory, or null
     int *carry;           // set once any deposit of this CTA carried into a high word
@@ -655,6 +659,41 @@ __device__ __forceinline__ void od_update(const FusedParams &p, int day, int od,
     }
 }
 
+// The solve's update of one OD for both tiles of a pair task (departures bA,
+// bB): the same arithmetic as od_update in SOLVE mode, with every global load of
+// both tiles (accumulator, flow, route choice) issued before the first use, so
+// that the pair pays one memory latency instead of a chain of them.
+template <int PREC, class RouteK, class RouteGp2>
+__device__ __forceinline__ void od_step2(const FusedParams &p, int day, int od, int bA, int bB, bool vwA, bool vwB,
+                                         int nr, RouteK route_k, RouteGp2 route_gp2) {
+    const float *pt = p.pt + (size_t)day * p.P * p.Np;
+    const size_t row = ((size_t)day * p.K + od) * p.Np;
+    const size_t qA = row + (vwA ? bA : 0), qB = row + (vwB ? bB : 0);
+    const float GA = p.G[qA], GB = p.G[qB], xA = p.q[qA], xB = p.q[qB];
+    float gA = 0.f, gB = 0.f;
+    for (int i = 0; i < nr; ++i) {
+        const float *pk = pt + (size_t)route_k(i) * p.Np;
+        const float pa = __ldg(&pk[vwA ? bA : 0]), pb = __ldg(&pk[vwB ? bB : 0]);
+        const float2 gp = route_gp2(i);
+        gA += pa * gp.x;
+        gB += pb * gp.y;
+    }
+    if (vwA) {
+        const float Gv = GA + gA * gA;
+        const float qv = fmaxf(xA - p.eta * gA / (sqrtf(Gv) + p.eps), 0.f);
+        p.G[qA] = Gv;
+        p.q[qA] = qv;
+        if (PREC == 1) p.qb[qA] = __float2bfloat16_rn(qv);
+    }
+    if (vwB) {
+        const float Gv = GB + gB * gB;
+        const float qv = fmaxf(xB - p.eta * gB / (sqrtf(Gv) + p.eps), 0.f);
+        p.G[qB] = Gv;
+        p.q[qB] = qv;
+        if (PREC == 1) p.qb[qB] = __float2bfloat16_rn(qv);
+    }
+}
+
 __device__ __forceinline__ void add_dtheta(double dth, double *s_dth) {
     for (int off = 16; off > 0; off >>= 1) dth += __shfl_down_sync(0xffffffffu, dth, off);
     if ((threadIdx.x & 31) == 0) atomicAdd(s_dth, dth);
@@ -737,16 +776,16 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
         gpl[t] = G;
         if (!((gr.w >> 8) & 1) && vw) gp[(size_t)k * p.Np + b] = G;
     }
-    const int e0 = __ldg(&p.god_ptr[g]), e1 = __ldg(&p.god_ptr[g + 1]);
+    const int e0 = s.god_ptr[g], e1 = s.god_ptr[g + 1];
     if (e0 == e1) return;
     double dth = 0.0;
     if (vw) {
         for (int e = e0; e < e1; ++e) {
-            const int r0 = __ldg(&p.godr_ptr[e]);
-            const int *gr = p.godr + r0;
-            od_update<PREC>(p, day, __ldg(&p.god[e]), b, __ldg(&p.godr_ptr[e + 1]) - r0,
-                            [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
-                            [&](int i) { return gpl[__ldg(&gr[i])]; }, dth);
+            const int r0 = s.godr_ptr[e];
+            const int *gr = s.godr + r0;
+            od_update<PREC>(p, day, s.god[e], b, s.godr_ptr[e + 1] - r0,
+                            [&](int i) { return s.groute[i0 + gr[i]].x; }, [&](int i) { return gpl[gr[i]]; },
+                            dth);
         }
     }
     if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
@@ -866,19 +905,28 @@ __device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, in
             if (vwB) gp[(size_t)k * p.Np + bB] = GB;
         }
     }
-    const int e0 = __ldg(&p.god_ptr[g]), e1 = __ldg(&p.god_ptr[g + 1]);
+    const int e0 = s.god_ptr[g], e1 = s.god_ptr[g + 1];
     if (e0 == e1) return;
+    if (p.mode == MODE_SOLVE) {
+        for (int e = e0; e < e1; ++e) {
+            const int r0 = s.godr_ptr[e];
+            const int *gr = s.godr + r0;
+            od_step2<PREC>(p, day, s.god[e], bA, bB, vwA, vwB, s.godr_ptr[e + 1] - r0,
+                           [&](int i) { return s.groute[i0 + gr[i]].x; }, [&](int i) { return gpl2[gr[i]]; });
+        }
+        return;
+    }
     double dth = 0.0;
     for (int e = e0; e < e1; ++e) {
-        const int r0 = __ldg(&p.godr_ptr[e]);
-        const int *gr = p.godr + r0;
-        const int od = __ldg(&p.god[e]), nr = __ldg(&p.godr_ptr[e + 1]) - r0;
+        const int r0 = s.godr_ptr[e];
+        const int *gr = s.godr + r0;
+        const int od = s.god[e], nr = s.godr_ptr[e + 1] - r0;
         if (vwA)
-            od_update<PREC>(p, day, od, bA, nr, [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
-                            [&](int i) { return gpl2[__ldg(&gr[i])].x; }, dth);
+            od_update<PREC>(p, day, od, bA, nr, [&](int i) { return s.groute[i0 + gr[i]].x; },
+                            [&](int i) { return gpl2[gr[i]].x; }, dth);
         if (vwB)
-            od_update<PREC>(p, day, od, bB, nr, [&](int i) { return s.groute[i0 + __ldg(&gr[i])].x; },
-                            [&](int i) { return gpl2[__ldg(&gr[i])].y; }, dth);
+            od_update<PREC>(p, day, od, bB, nr, [&](int i) { return s.groute[i0 + gr[i]].x; },
+                            [&](int i) { return gpl2[gr[i]].y; }, dth);
     }
     if (p.mode == MODE_LOSS_GRAD) add_dtheta(dth, s_dth);
 }
@@ -1134,64 +1182,86 @@ __device__ __forceinline__ void flush_phase(const FusedParams &p, const Shared &
 }
 
 // Solve-path flush of a phase (the !EXACT case of flush_phase), four rows per
-// thread: 16-byte loads of counts (and row-chunk labels) at 4-aligned row
-// positions, one mask word, 8- or 16-byte residual stores.
+// chunk: 16-byte loads of counts (and row-chunk labels) at 4-aligned row
+// positions, one mask word, 8- or 16-byte residual stores.  Each thread issues
+// the loads of U chunks before using any of them (one memory latency per U
+// chunks); chunks are summed in the same order as one at a time.
 template <int PREC, bool SMEM_RING>
 __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &s, float *gacc, void *rb,
                                             const float *cnt, const uint32_t *mk, const int32_t *lab, int sel, int pb0,
                                             int rows, bool carry, float &ks, float &kc) {
+    constexpr int U = 4;                  // chunks per thread whose loads are in flight together
     const int c0 = pb0 & ~3;
     const int nch = (pb0 + rows - c0 + 3) >> 2;
     const int total = p.O * nch;
-    for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int o = i / nch, c = c0 + 4 * (i - o * nch);
-        const size_t cell = (size_t)o * p.Np + c;
-        const float4 cv = __ldg(reinterpret_cast<const float4 *>(cnt + cell));
-        const uint32_t mw = (__ldg(&mk[(size_t)o * p.Nw + (c >> 5)]) >> (c & 31)) & 0xfu;
-        int4 lv = make_int4(0, 0, 0, 0);
-        if (sel >= 0) lv = __ldcg(reinterpret_cast<const int4 *>(lab + cell));
-        const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
-        const int ll[4] = {lv.x, lv.y, lv.z, lv.w};
-        float r4[4];
+    for (int i0 = threadIdx.x; i0 < total; i0 += U * blockDim.x) {
+        float4 cv[U];
+        uint32_t mw[U];
+        int4 lv[U];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int r = c + k - pb0;
-            const bool in = r >= 0 && r < rows;
-            float x = 0.f;
-            if (in) {
-                if (SMEM_RING) {
-                    const int idx = o * s.R + r;
-                    const int hw = carry ? s.hi[idx] : 0;
-                    x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
-                } else {
-                    x = gacc[cell + k];
-                    gacc[cell + k] = 0.f;
-                }
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            mw[u] = 0u;
+            lv[u] = make_int4(0, 0, 0, 0);
+            if (i < total) {
+                const int o = i / nch, c = c0 + 4 * (i - o * nch);
+                const size_t cell = (size_t)o * p.Np + c;
+                cv[u] = __ldg(reinterpret_cast<const float4 *>(cnt + cell));
+                mw[u] = (__ldg(&mk[(size_t)o * p.Nw + (c >> 5)]) >> (c & 31)) & 0xfu;
+                if (sel >= 0) lv[u] = __ldcg(reinterpret_cast<const int4 *>(lab + cell));
             }
-            const bool on = in && ((mw >> k) & 1u);
-            const float rr = on ? x - cc[k] : 0.f;
-            const float y = rr * rr - kc;          // compensated (Kahan) sum
-            const float t = ks + y;
-            kc = (t - ks) - y;
-            ks = t;
-            r4[k] = (sel < 0 || (on && ll[k] == sel)) ? rr : 0.f;
         }
-        if (c >= pb0 && c + 4 <= pb0 + rows) {
-            if (PREC == 1) {
-                __nv_bfloat162 lo2 = __floats2bfloat162_rn(r4[0], r4[1]);
-                __nv_bfloat162 hi2 = __floats2bfloat162_rn(r4[2], r4[3]);
-                uint2 pk;
-                pk.x = *reinterpret_cast<uint32_t *>(&lo2);
-                pk.y = *reinterpret_cast<uint32_t *>(&hi2);
-                *reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(rb) + cell) = pk;
-            } else {
-                *reinterpret_cast<float4 *>(static_cast<float *>(rb) + cell) = make_float4(r4[0], r4[1], r4[2], r4[3]);
-            }
-        } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= total) continue;
+            const int o = i / nch, c = c0 + 4 * (i - o * nch);
+            const size_t cell = (size_t)o * p.Np + c;
+            const float cc[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+            const int ll[4] = {lv[u].x, lv[u].y, lv[u].z, lv[u].w};
+            float r4[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int r = c + k - pb0;
-                if (r >= 0 && r < rows) Operand<PREC>::store_r(rb, cell + k, r4[k]);
+                const bool in = r >= 0 && r < rows;
+                float x = 0.f;
+                if (in) {
+                    if (SMEM_RING) {
+                        const int idx = o * s.R + r;
+                        const int hw = carry ? s.hi[idx] : 0;
+                        x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
+                    } else {
+                        x = gacc[cell + k];
+                        gacc[cell + k] = 0.f;
+                    }
+                }
+                const bool on = in && ((mw[u] >> k) & 1u);
+                const float rr = on ? x - cc[k] : 0.f;
+                const float y = rr * rr - kc;          // compensated (Kahan) sum
+                const float t = ks + y;
+                kc = (t - ks) - y;
+                ks = t;
+                r4[k] = (sel < 0 || (on && ll[k] == sel)) ? rr : 0.f;
+            }
+            if (c >= pb0 && c + 4 <= pb0 + rows) {
+                if (PREC == 1) {
+                    __nv_bfloat162 lo2 = __floats2bfloat162_rn(r4[0], r4[1]);
+                    __nv_bfloat162 hi2 = __floats2bfloat162_rn(r4[2], r4[3]);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<uint32_t *>(&lo2);
+                    pk.y = *reinterpret_cast<uint32_t *>(&hi2);
+                    *reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(rb) + cell) = pk;
+                } else {
+                    *reinterpret_cast<float4 *>(static_cast<float *>(rb) + cell) =
+                        make_float4(r4[0], r4[1], r4[2], r4[3]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = c + k - pb0;
+                    if (r >= 0 && r < rows) Operand<PREC>::store_r(rb, cell + k, r4[k]);
+                }
             }
         }
     }
@@ -1311,7 +1381,8 @@ __device__ __forceinline__ TaskRef task_ref(int t, int nt, int nb, int pb0, cons
 }
 
 // Dynamic shared memory layout (16-byte aligned blocks):
-//   groute int4[P] | gptr int[G+1] | task_grp int[G] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
+//   groute int4[P] | gptr int[G+1] | task_grp int[G] |
+//   OD tables int[G+1 + n_god + n_god+1 + n_godr] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
 __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1327,6 +1398,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     off = align16(off + (size_t)(p.n_groups + 1) * sizeof(int));
     int *task_grp = reinterpret_cast<int *>(smem_raw + off);
     off = align16(off + (size_t)p.n_groups * sizeof(int));
+    int *odt = reinterpret_cast<int *>(smem_raw + off);
+    off = align16(off + (size_t)(p.n_groups + 1 + 2 * p.n_god + 1 + p.n_godr) * sizeof(int));
     uint32_t *colact = reinterpret_cast<uint32_t *>(smem_raw + off);
     off = align16(off + (size_t)p.Ow * sizeof(uint32_t));
     s.lo = reinterpret_cast<uint32_t *>(smem_raw + off);
@@ -1336,6 +1409,10 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     s.groute = groute;
     s.gptr = gptr;
     s.task_grp = task_grp;
+    s.god_ptr = odt;
+    s.god = odt + p.n_groups + 1;
+    s.godr_ptr = odt + p.n_groups + 1 + p.n_god;
+    s.godr = odt + p.n_groups + 1 + 2 * p.n_god + 1;
     s.rtab = (p.rtab_off >= 0 && !p.rtab_packed) ? reinterpret_cast<const int2 *>(smem_raw + p.rtab_off) : nullptr;
     s.rtab32 = (p.rtab_off >= 0 && p.rtab_packed) ? reinterpret_cast<const uint32_t *>(smem_raw + p.rtab_off) : nullptr;
     s.hi = SMEM_RING ? reinterpret_cast<int *>(p.gring) + (size_t)blockIdx.x * p.O * s.R : nullptr;
@@ -1358,6 +1435,11 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     for (int i = threadIdx.x; i < p.P; i += nthr) groute[i] = __ldg(&p.groute[i]);
     for (int i = threadIdx.x; i <= p.n_groups; i += nthr) gptr[i] = __ldg(&p.gptr[i]);
     for (int i = threadIdx.x; i < p.n_groups; i += nthr) task_grp[i] = __ldg(&p.task_grp[i]);
+    for (int i = threadIdx.x; i <= p.n_groups; i += nthr) odt[i] = __ldg(&p.god_ptr[i]);
+    for (int i = threadIdx.x; i < p.n_god; i += nthr) odt[p.n_groups + 1 + i] = __ldg(&p.god[i]);
+    for (int i = threadIdx.x; i <= p.n_god; i += nthr) odt[p.n_groups + 1 + p.n_god + i] = __ldg(&p.godr_ptr[i]);
+    for (int i = threadIdx.x; i < p.n_godr; i += nthr)
+        odt[p.n_groups + 1 + 2 * p.n_god + 1 + i] = __ldg(&p.godr[i]);
     if (p.rtab_off >= 0 && p.rtab_packed) {
         uint32_t *rt = reinterpret_cast<uint32_t *>(smem_raw + p.rtab_off);
         for (int i = threadIdx.x; i < p.rptr_total; i += nthr) rt[i] = __ldg(&p.rtab32[i]);

@@ -30,7 +30,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 # every entry point of include/dode.h
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
-           "dode_loss_grad", "dode_last_totals", "dode_dense_nnls", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
+           "dode_loss_grad", "dode_last_totals", "dode_dense_nnls", "dode_dense_set_wait_limit", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
            "dode_last_kernel_ms", "dode_last_launches", "dode_last_grid", "dode_total_launches", "dode_device", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH):
         "dode_loss_grad": (ct.c_int, [vp, vp, f32, vp, vp, vp, i32]),
         "dode_last_totals": (ct.c_int, [vp, vp, vp]),
         "dode_dense_nnls": (ct.c_int, [i32, i32, i32, vp, vp, i32, f32, f32, i32, vp, vp, vp, vp, i32, vp]),
+        "dode_dense_set_wait_limit": (ct.c_int, [i64]),
         "dode_set_patterns": (ct.c_int, [vp, vp]),
         "dode_r2": (ct.c_int, [vp, vp, f32, vp, i32]),
         "dode_dar_distance": (ct.c_int, [vp, vp, vp]),
@@ -452,3 +453,10 @@ def dense_nnls(B, Y, iters: int, step: float, X0=None, G0=None, eps: float = 1e-
     if rc != OK:
         raise DodeError(rc, "dode_dense_nnls failed (details on stderr)")
     return X, G, loss, ms.value
+
+
+def dense_set_wait_limit(polls: int) -> None:
+    """``dode_dense_set_wait_limit``: polls of the one-pass dense kernel's bounded waits (default 2^26)."""
+    rc = load().dode_dense_set_wait_limit(int(polls))
+    if rc != OK:
+        raise DodeError(rc, "dode_dense_set_wait_limit: polls must be >= 0")

@@ -48,8 +48,8 @@ def test_algorithmic_bytes_of_the_3yr_corridor():
 
 
 def test_measured_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
-    """The ncu figures are reported only for the workload, precision and kernel
-    source they were taken of (the source matched by its hash)."""
+    """The ncu figures are reported only for the form, workload, precision and
+    kernel source they were taken of (the source matched by its hash)."""
     import hashlib
 
     import bench
@@ -58,19 +58,24 @@ def test_measured_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     kernel = b"// a kernel source\n"
     (src / "fused.cu").write_bytes(kernel)
-    (tmp_path / "profiles" / "fused_kernel_corridor-3yr-152d_traffic.txt").write_text(
+    (tmp_path / "profiles" / "fused_kernel_fp32_corridor-3yr-152d_traffic.txt").write_text(
         "# a capture\n"
-        "kernel = k_fused<1,1,1> (BF16 form)\n"
-        f"fused_cu_sha256_16 = {hashlib.sha256(kernel).hexdigest()[:16]}\n"
+        "kernel = k_fused<0,1,1> (FP32 form)\n"
+        "form = fused\n"
+        "workload = corridor-3yr\n"
+        "precision = fp32\n"
+        "source = paper_1901_09266_gb300/csrc/fused.cu\n"
+        f"source_sha256_16 = {hashlib.sha256(kernel).hexdigest()[:16]}\n"
         "bytes_per_day_iteration = 4398377\n"
         "warp_instructions_per_day_iteration = 3304333\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.measured_traffic("corridor-3yr", "bf16") == 4398377.0
-    assert bench.measured_traffic("corridor-3yr", "bf16", "warp_instructions_per_day_iteration") == 3304333.0
-    assert bench.measured_traffic("corridor-3yr", "fp32") is None
-    assert bench.measured_traffic("corridor-large", "bf16") is None
+    assert bench.measured_traffic("fused", "corridor-3yr", "fp32") == 4398377.0
+    assert bench.measured_traffic("fused", "corridor-3yr", "fp32", "warp_instructions_per_day_iteration") == 3304333.0
+    assert bench.measured_traffic("fused", "corridor-3yr", "bf16") is None
+    assert bench.measured_traffic("plain", "corridor-3yr", "fp32") is None
+    assert bench.measured_traffic("fused", "corridor-large", "fp32") is None
     (src / "fused.cu").write_bytes(kernel + b"// changed\n")
-    assert bench.measured_traffic("corridor-3yr", "bf16") is None
+    assert bench.measured_traffic("fused", "corridor-3yr", "fp32") is None
 
 
 def test_clock_sampler_reads_clocks_and_throttle_reasons(tmp_path, monkeypatch):

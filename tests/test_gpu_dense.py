@@ -75,3 +75,24 @@ def test_dense_one_pass_matches_two_passes_and_oracle(nr, nc):
     with pytest.raises(dode.DodeError) as e:
         dode.dense_nnls(B, np.concatenate([Y, Y], axis=1), 1, 0.05, method=1)
     assert e.value.code == dode.ERR_UNSUPPORTED
+
+
+def test_dense_one_pass_wait_runs_out_then_recovers():
+    """Failure path of the one-pass kernel without a GPU fault: with a wait limit
+    of 0 polls every bounded wait for a row copy gives up at once, the call
+    returns DODE_ERR_DEVICE_TIMEOUT after the kernel let its copies in flight
+    land, and the next call in the same process matches the oracle."""
+    B, Y = _instance(1003, 1024, 1, seed=9)
+    dode.dense_set_wait_limit(0)
+    try:
+        with pytest.raises(dode.DodeError) as e:
+            dode.dense_nnls(B, Y, 5, 0.05, method=1)
+        assert e.value.code == dode.ERR_DEVICE_TIMEOUT
+    finally:
+        dode.dense_set_wait_limit(1 << 26)
+    X, _, loss, _ = dode.dense_nnls(B, Y, 20, 0.05, method=1)
+    Xo, _, lo = spgd_dense(B, Y, 20, 0.05)
+    np.testing.assert_allclose(loss, lo, rtol=1e-5)
+    assert rel_norm(X, Xo, axis=0).max() < 1e-4
+    with pytest.raises(dode.DodeError):
+        dode.dense_set_wait_limit(-1)
