@@ -1481,7 +1481,7 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
         return bail(DODE_ERR_UNSUPPORTED,
                     "one pass needs m = 1, n_cols % 4 == 0, n_cols <= 8192, 16-byte aligned B, cooperative launch");
     const bool one = method == 1 || (method == 0 && one_ok);
-    const int grid_f = n_sm;
+    const int grid_f = std::min(n_sm, 192);      // the one-pass step sums at most 192 partials per column
     // one device allocation: (B, y when on the host) x, G, r, gradient partials, loss
     // partials (of either kernel), loss, error flag; every piece starts on a
     // 256-byte boundary (the kernels use 16-byte accesses)

@@ -86,6 +86,15 @@ struct Operand<1> {
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
+// Lanes that share one row of a staging or flush loop: the smallest power of
+// two (at most 32) that covers the row's n chunks, as its log2.  A warp then
+// takes 32 >> lg rows at a time and no index needs a division.
+__device__ __forceinline__ int lane_group_log2(int n) { return n <= 1 ? 0 : min(5, 32 - __clz(n - 1)); }
+
+// i / n for 0 <= i < 2^31 by the multiply-high of IntervalDiv (d = make_interval_div(max(n, 2))).
+__device__ __forceinline__ int div_by(int i, int n, const IntervalDiv &d) { return n == 1 ? i : interval_of(i, d); }
+
+
 struct Shared {
     uint32_t *lo;         // [O][R]: accumulator low words (forward) / residual window as float bits (adjoint)
     int *hi;              // [O][R] in global memory: accumulator high words (forward)
@@ -979,6 +988,7 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
                                             const uint16_t *t16n) {
     const int c0 = s.pb & ~7;
     const int nch = (s.pb + s.RW - c0 + 7) >> 3;       // 8-tick chunks per link
+    const IntervalDiv dn = make_interval_div(max(nch, 2));
     const int total = p.A * nch;
     for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
         uint4 v[4];
@@ -987,7 +997,7 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
             const int i = i0 + u * blockDim.x;
             v[u] = make_uint4(0u, 0u, 0u, 0u);
             if (i < total) {
-                const int a = i / nch, c = c0 + 8 * (i - a * nch);
+                const int a = div_by(i, nch, dn), c = c0 + 8 * (i - a * nch);
                 const uint16_t *row = t16 + (size_t)a * p.Np;
                 if (c + 8 <= (t16n ? p.N : p.Np)) {
                     v[u] = __ldg(reinterpret_cast<const uint4 *>(row + c));
@@ -1012,7 +1022,7 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + u * blockDim.x;
             if (i < total) {
-                const int a = i / nch, c = c0 + 8 * (i - a * nch);
+                const int a = div_by(i, nch, dn), c = c0 + 8 * (i - a * nch);
                 const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
                 uint16_t *row = s.tw + a * s.RW;
 #pragma unroll
@@ -1058,6 +1068,7 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
     const int rows = min(s.R, p.N - s.pb);
     const int c0 = s.pb & ~(E - 1);
     const int nch = (s.pb + rows - c0 + E - 1) / E;
+    const IntervalDiv dn = make_interval_div(max(nch, 2));
     const int total = p.O * nch;
     for (int i0 = threadIdx.x; i0 < total; i0 += 4 * blockDim.x) {
         uint4 v[4];
@@ -1066,7 +1077,7 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
             const int i = i0 + u * blockDim.x;
             v[u] = make_uint4(0u, 0u, 0u, 0u);
             if (i < total) {
-                const int o = i / nch, c = c0 + E * (i - o * nch);
+                const int o = div_by(i, nch, dn), c = c0 + E * (i - o * nch);
                 v[u] = __ldcg(reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(rb) +
                                                             ((size_t)o * p.Np + c) * (PREC == 1 ? 2 : 4)));
             }
@@ -1075,7 +1086,7 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + u * blockDim.x;
             if (i < total) {
-                const int o = i / nch, c = c0 + E * (i - o * nch);
+                const int o = div_by(i, nch, dn), c = c0 + E * (i - o * nch);
                 const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
                 uint32_t *row = s.lo + o * s.R;
 #pragma unroll
@@ -1185,14 +1196,16 @@ __device__ __forceinline__ void flush_phase(const FusedParams &p, const Shared &
 // chunk: 16-byte loads of counts (and row-chunk labels) at 4-aligned row
 // positions, one mask word, 8- or 16-byte residual stores.  Each thread issues
 // the loads of U chunks before using any of them (one memory latency per U
-// chunks); chunks are summed in the same order as one at a time.
+// chunks, U kept small for the registers); chunks are summed in the same order
+// as one at a time.
 template <int PREC, bool SMEM_RING>
 __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &s, float *gacc, void *rb,
                                             const float *cnt, const uint32_t *mk, const int32_t *lab, int sel, int pb0,
                                             int rows, bool carry, float &ks, float &kc) {
-    constexpr int U = 4;                  // chunks per thread whose loads are in flight together
+    constexpr int U = 2;                  // chunks per thread whose loads are in flight together
     const int c0 = pb0 & ~3;
     const int nch = (pb0 + rows - c0 + 3) >> 2;
+    const IntervalDiv dn = make_interval_div(max(nch, 2));
     const int total = p.O * nch;
     for (int i0 = threadIdx.x; i0 < total; i0 += U * blockDim.x) {
         float4 cv[U];
@@ -1205,7 +1218,7 @@ __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &
             mw[u] = 0u;
             lv[u] = make_int4(0, 0, 0, 0);
             if (i < total) {
-                const int o = i / nch, c = c0 + 4 * (i - o * nch);
+                const int o = div_by(i, nch, dn), c = c0 + 4 * (i - o * nch);
                 const size_t cell = (size_t)o * p.Np + c;
                 cv[u] = __ldg(reinterpret_cast<const float4 *>(cnt + cell));
                 mw[u] = (__ldg(&mk[(size_t)o * p.Nw + (c >> 5)]) >> (c & 31)) & 0xfu;
@@ -1216,7 +1229,7 @@ __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &
         for (int u = 0; u < U; ++u) {
             const int i = i0 + u * blockDim.x;
             if (i >= total) continue;
-            const int o = i / nch, c = c0 + 4 * (i - o * nch);
+            const int o = div_by(i, nch, dn), c = c0 + 4 * (i - o * nch);
             const size_t cell = (size_t)o * p.Np + c;
             const float cc[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
             const int ll[4] = {lv[u].x, lv[u].y, lv[u].z, lv[u].w};
@@ -1264,6 +1277,114 @@ __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &
                 }
             }
         }
+    }
+}
+
+// Solve-path flush of a phase on the shared ring, fused with the move of its
+// spill rows.  Each observed link's ring row belongs to one group of lanes of
+// one warp (4-cell chunks at 4-aligned row positions), so no other warp touches
+// it and the move needs no CTA barrier.  Every cell of rows [0, span) is read
+// and cleared; rows [0, rows) become masked residuals r = m (xhat - x) (Eq.
+// (nnls)), summed into the loss with a compensated FP32 sum and written to the
+// residual slot; then the spill rows [span, span + spill) move to [0, spill) and
+// are cleared.  The loads of U rows are in flight together.
+template <int PREC>
+__device__ __forceinline__ void flush_move_solve(const FusedParams &p, const Shared &s, void *rb, const float *cnt,
+                                                 const uint32_t *mk, const int32_t *lab, int sel, int pb0, int rows,
+                                                 int span, int spill, bool carry, float &ks, float &kc) {
+    constexpr int U = 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c0 = pb0 & ~3;
+    const int nch = (pb0 + span - c0 + 3) >> 2;          // chunks covering rows [0, span)
+    const int lg = lane_group_log2(nch);
+    const int L = 1 << lg, per = 32 >> lg;
+    const int sub = lane >> lg, kq = lane & (L - 1);
+    const int step = nw * per;
+    for (int o0 = warp * per; o0 < p.O; o0 += U * step) {
+        for (int k0 = 0; k0 < nch; k0 += L) {
+            const int k = k0 + kq, c = c0 + 4 * k;
+            float4 cv[U];
+            uint32_t mw[U];
+            int4 lv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int o = o0 + u * step + sub;
+                cv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                mw[u] = 0u;
+                lv[u] = make_int4(0, 0, 0, 0);
+                if (o < p.O && k < nch && c < pb0 + rows) {
+                    const size_t cell = (size_t)o * p.Np + c;
+                    cv[u] = __ldg(reinterpret_cast<const float4 *>(cnt + cell));
+                    mw[u] = (__ldg(&mk[(size_t)o * p.Nw + (c >> 5)]) >> (c & 31)) & 0xfu;
+                    if (sel >= 0) lv[u] = __ldcg(reinterpret_cast<const int4 *>(lab + cell));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int o = o0 + u * step + sub;
+                if (o >= p.O || k >= nch) continue;
+                const size_t cell = (size_t)o * p.Np + c;
+                const float cc[4] = {cv[u].x, cv[u].y, cv[u].z, cv[u].w};
+                const int ll[4] = {lv[u].x, lv[u].y, lv[u].z, lv[u].w};
+                float r4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = c + q - pb0;
+                    float x = 0.f;
+                    if (r >= 0 && r < span) {
+                        const int idx = o * s.R + r;
+                        const int hw = carry ? s.hi[idx] : 0;
+                        x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
+                        s.lo[idx] = 0u;
+                        if (carry) s.hi[idx] = 0;
+                    }
+                    const bool on = r >= 0 && r < rows && ((mw[u] >> q) & 1u);
+                    const float rr = on ? x - cc[q] : 0.f;
+                    const float y = rr * rr - kc;          // compensated (Kahan) sum
+                    const float t = ks + y;
+                    kc = (t - ks) - y;
+                    ks = t;
+                    r4[q] = (sel < 0 || (on && ll[q] == sel)) ? rr : 0.f;
+                }
+                if (c >= pb0 && c + 4 <= pb0 + rows) {
+                    if (PREC == 1) {
+                        __nv_bfloat162 lo2 = __floats2bfloat162_rn(r4[0], r4[1]);
+                        __nv_bfloat162 hi2 = __floats2bfloat162_rn(r4[2], r4[3]);
+                        uint2 pk;
+                        pk.x = *reinterpret_cast<uint32_t *>(&lo2);
+                        pk.y = *reinterpret_cast<uint32_t *>(&hi2);
+                        *reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(rb) + cell) = pk;
+                    } else {
+                        *reinterpret_cast<float4 *>(static_cast<float *>(rb) + cell) =
+                            make_float4(r4[0], r4[1], r4[2], r4[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = c + q - pb0;
+                        if (r >= 0 && r < rows) Operand<PREC>::store_r(rb, cell + q, r4[q]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // spill rows to the front of each row this warp flushed
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int o = o0 + u * step + sub;
+            if (o >= p.O) continue;
+            uint32_t *lrow = s.lo + o * s.R;
+            int *hrow = s.hi + o * s.R;
+            for (int r = kq; r < spill; r += L) {
+                lrow[r] = lrow[span + r];
+                lrow[span + r] = 0u;
+                if (carry) {
+                    hrow[r] = hrow[span + r];
+                    hrow[span + r] = 0;
+                }
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -1591,6 +1712,8 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                 } else if (exact)
                     flush_phase<PREC, SMEM_RING, true>(p, s, gacc, rb, cnt, mk, lab, sel, day, pb0, rows, carry, lsum,
                                                        ks, kc);
+                else if (SMEM_RING)
+                    flush_move_solve<PREC>(p, s, rb, cnt, mk, lab, sel, pb0, rows, span, spill, carry, ks, kc);
                 else
                     flush_solve<PREC, SMEM_RING>(p, s, gacc, rb, cnt, mk, lab, sel, pb0, rows, carry, ks, kc);
                 if (SMEM_TICKS && !tab && !halo_pass && pb0 + adv < p.N) {
@@ -1600,8 +1723,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
                     tw_pb = pb0 + adv;
                     s.pb = pb0;
                 }
-                if (SMEM_RING) {
+                if (SMEM_RING && (halo_pass || exact)) {
                     // move the spill rows [span, span + spill) to the front, zero the rest
+                    // (the solve's flush has done both for the rows it flushed)
                     __syncthreads();
                     for (int o = warp; o < p.O; o += nwarps) {
                         uint32_t *lrow = s.lo + o * s.R;
