@@ -550,13 +550,36 @@ def run_gpu(args):
         Yd = Bd @ torch.from_numpy(xt).to(dev)
         dode.dense_nnls(Bd, Yd, 3, 0.05)                                   # warm-up
         _, _, ld, ms_dense = dode.dense_nnls(Bd, Yd, args.dense_iters, 0.05)
-        per = ms_dense / (args.dense_iters + 0.5)                         # + the final residual pass
+        per = ms_dense / (args.dense_iters + 1)                           # + the final residual pass (one more pass over B)
         nxt["dense_nnls"] = {"n": n, "m": 1, "iters": args.dense_iters, "ms_per_iter": per,
                              "roofline": {"bound": "hbm", "achieved": 4.0 * n * n / (per / 1e3) / 1e9,
                                           "peak": peaks.get("hbm_gbs") or 6800.0, "unit": "GB/s",
                                           "frac": 4.0 * n * n / (per / 1e3) / 1e9 / (peaks.get("hbm_gbs") or 6800.0),
                                           "bytes_per_iter": 4 * n * n, "method": "one pass over B"},
                              "final_loss": float(ld.sum().item())}
+        # many right-hand sides sharing B: the two products as TF32 GEMMs on the
+        # tensor cores (method 3); each iteration reads B and its transpose once
+        tc = []
+        for m_tc in args.dense_tc_m:
+            Xs = np.abs(rng.standard_normal((n, m_tc))).astype(np.float32)
+            Yt = Bd @ torch.from_numpy(Xs).to(dev)
+            dode.dense_nnls(Bd, Yt, 2, 0.05, method=3)                    # warm-up
+            _, _, lt, ms_tc = dode.dense_nnls(Bd, Yt, args.dense_iters, 0.05, method=3)
+            per_tc = ms_tc / (args.dense_iters + 0.5)                      # + the final residual GEMM
+            flops = 4.0 * n * n * m_tc
+            pk_tf = (peaks.get("bf16_tflops") or 1900.0) / 2.0          # TF32 = half the BF16 rate (nominal ratio)
+            tc.append({"m": m_tc, "ms_per_iter": per_tc, "tflops": flops / (per_tc / 1e3) / 1e12,
+                       "roofline": {"bound": "hbm", "achieved": 8.0 * n * n / (per_tc / 1e3) / 1e9,
+                                    "peak": peaks.get("hbm_gbs") or 6800.0, "unit": "GB/s",
+                                    "frac": 8.0 * n * n / (per_tc / 1e3) / 1e9 / (peaks.get("hbm_gbs") or 6800.0),
+                                    "bytes_per_iter": 8 * n * n, "method": "B and B^T once each (TF32 GEMMs)"},
+                       "tensor_roofline": {"bound": "tensor", "achieved": flops / (per_tc / 1e3) / 1e12,
+                                           "peak": pk_tf, "unit": "TFLOP/s",
+                                           "frac": flops / (per_tc / 1e3) / 1e12 / pk_tf,
+                                           "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1/2"},
+                       "right_hand_side_iters_per_s": m_tc / (per_tc / 1e3),
+                       "final_loss": float(lt.sum().item())})
+        nxt["dense_nnls"]["tensor_cores"] = tc
         del Bd, Yd
 
     # form 3 (differentiable) on the 600-OD / 1500-route / 1000-detector corridor:
@@ -674,6 +697,8 @@ def main(argv=None):
     ap.add_argument("--uneven-epochs", type=int, default=50)
     ap.add_argument("--dense-n", type=int, default=6000)
     ap.add_argument("--dense-iters", type=int, default=50)
+    ap.add_argument("--dense-tc-m", type=lambda v: [int(x) for x in v.split(",")] if v else [], default=[64, 256],
+                    help="right-hand sides of the tensor-core dense timing (multiples of 16; empty = skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-days", type=int, default=1096)
     ap.add_argument("--ref-epochs", type=int, default=20)

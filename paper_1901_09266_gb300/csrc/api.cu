@@ -1428,6 +1428,61 @@ int dode_loss(dode_ctx *ctx, const float *q, float theta, double *loss, int32_t 
     return DODE_OK;
 }
 
+// Method 3 of dode_dense_nnls: the m right-hand sides stacked into GEMMs on the
+// tensor cores (dense_tc.cu), TF32 products with FP32 accumulation.
+static int dense_nnls_tc(int32_t nr, int32_t nc, int32_t m, const float *B, const float *Y, int32_t iters, float step,
+                         float eps, float *X, float *G, double *loss, double *kernel_ms, int32_t ptr_kind,
+                         void *stream) {
+    auto bail = [&](int code, const std::string &msg) {
+        fprintf(stderr, "dode_dense_nnls: %s\n", msg.c_str());
+        return code;
+    };
+    const bool host = ptr_kind == DODE_PTR_HOST;
+    if (m % 16 != 0 || nr % 4 != 0 || nc % 4 != 0 || (!host && ((uintptr_t)B % 16 || (uintptr_t)Y % 16)))
+        return bail(DODE_ERR_UNSUPPORTED,
+                    "tensor cores need m a multiple of 16 (16..256), n_rows and n_cols multiples of 4, 16-byte "
+                    "aligned B and Y");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t nB = (size_t)nr * nc, nY = (size_t)nr * m, nX = (size_t)nc * m;
+    float *dB = nullptr, *dY = nullptr, *dX = nullptr, *dG = nullptr;
+    double *dl = nullptr;
+    const cudaMemcpyKind in = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    cudaError_t e = cudaSuccess;
+    if (host) {
+        e = cudaMalloc(&dB, nB * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&dY, nY * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dB, B, nB * 4, in, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dY, Y, nY * 4, in, st);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&dX, nX * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dG, nX * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dl, (size_t)m * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X, nX * 4, in, st);
+    if (e == cudaSuccess) e = G ? cudaMemcpyAsync(dG, G, nX * 4, in, st) : cudaMemsetAsync(dG, 0, nX * 4, st);
+    int rc = 0, herr = 0;
+    float ms = 0.f;
+    if (e == cudaSuccess)
+        rc = dense_tc_nnls(nr, nc, m, host ? dB : B, host ? dY : Y, iters, step, eps, dX, dG, dl, &ms, &herr, st);
+    const cudaMemcpyKind out = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (e == cudaSuccess && rc == 0) e = cudaMemcpyAsync(X, dX, nX * 4, out, st);
+    if (e == cudaSuccess && rc == 0 && G) e = cudaMemcpyAsync(G, dG, nX * 4, out, st);
+    if (e == cudaSuccess && rc == 0) e = cudaMemcpyAsync(loss, dl, (size_t)m * sizeof(double), out, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dB);
+    cudaFree(dY);
+    cudaFree(dX);
+    cudaFree(dG);
+    cudaFree(dl);
+    if (e != cudaSuccess || rc != 0) {
+        (void)cudaGetLastError();
+        return bail(rc == -1 ? DODE_ERR_CUDA : (e == cudaErrorMemoryAllocation ? DODE_ERR_OOM : DODE_ERR_CUDA),
+                    e != cudaSuccess ? cudaGetErrorString(e) : "tensor-core path failed");
+    }
+    if (herr) return bail(DODE_ERR_DEVICE_TIMEOUT, "a bounded wait of the tensor-core kernel ran out");
+    if (kernel_ms) *kernel_ms = ms;
+    return DODE_OK;
+}
+
 // Polls of a bounded wait in the one-pass dense kernel before it gives up.
 static long long g_dense_wait_limit = 1ll << 26;
 
@@ -1444,10 +1499,12 @@ int dode_dense_nnls(int32_t n_rows, int32_t n_cols, int32_t m, const float *B, c
         fprintf(stderr, "dode_dense_nnls: %s\n", msg.c_str());
         return code;
     };
-    if (n_rows < 1 || n_cols < 1 || m < 1 || m > 8 || iters < 0 || !(step > 0.f) || !std::isfinite(step) ||
+    if (n_rows < 1 || n_cols < 1 || m < 1 || m > 256 || iters < 0 || !(step > 0.f) || !std::isfinite(step) ||
         !(eps >= 0.f) || !B || !Y || !X || !loss || (ptr_kind != DODE_PTR_HOST && ptr_kind != DODE_PTR_DEVICE) ||
-        method < 0 || method > 2)
-        return bail(DODE_ERR_ARG, "arguments (1 <= m <= 8, iters >= 0, step > 0, method 0..2)");
+        method < 0 || method > 3 || (m > 8 && method != 3))
+        return bail(DODE_ERR_ARG, "arguments (1 <= m <= 8, or <= 256 with method 3; iters >= 0, step > 0, method 0..3)");
+    if (method == 3) return dense_nnls_tc(n_rows, n_cols, m, B, Y, iters, step, eps, X, G, loss, kernel_ms, ptr_kind,
+                                          stream);
     if ((long long)n_cols * m * sizeof(float) > 200 * 1024)
         return bail(DODE_ERR_UNSUPPORTED, "n_cols * m must be at most 51200 (x is staged in shared memory)");
     int dev = 0, n_sm = 0;

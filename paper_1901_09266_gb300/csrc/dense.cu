@@ -180,9 +180,7 @@ __global__ void k_dense_loss(const double *__restrict__ lpart, int n_part, int m
 // Warp roles, synchronised by mbarriers only:
 //   warp 8      producer: one lane issues row copies into free stages
 //               (full[s] completes when the row has landed; empty[s] when the
-//               consumers are done with the stage), and L2 prefetches of the
-//               rows kPersistAhead copies ahead, which keep DRAM busy while the
-//               ring is full (through the grid-wide step)
+//               consumers are done with the stage)
 //   warps 0..3  residuals: warp w takes the row copies q = w mod 4 (counted
 //               over the whole launch) and forms r_j = B_j . x - y_j from shared
 //               memory (a warp sum), publishing it through rready[s]
@@ -201,8 +199,6 @@ constexpr int kPersistStages = 8;                   // ring stages (rows): 4 or 
 constexpr int kPersistStrips = 16;                  // n_cols <= 16 * 512
 constexpr int kPersistThreads = 288;                // 8 compute warps + 1 producer warp
 constexpr long long kDrainLimit = 1ll << 26;
-constexpr int kPersistAhead = 16;                  // rows prefetched into L2 ahead of the copy stream
-constexpr int kPersistParts = 24;                   // gradient partials per thread in the step: grid <= 192
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -244,7 +240,7 @@ __device__ bool grid_barrier(unsigned int *count, unsigned int k, const volatile
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
         if (v >= target) return true;
         if (*err) return false;
-        __nanosleep(32);
+        __nanosleep(64);
     }
     return false;
 }
@@ -307,13 +303,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                         smem_u32(dst)),
                     "l"(src), "r"(bytes), "r"(smem_u32(&full[st]))
                     : "memory");
-                // keep DRAM busy past the ring: the row kPersistAhead copies ahead
-                // goes to L2 now (it is read at most once more before it is copied)
-                if (q + kPersistAhead < nseq)
-                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
-                                     p.B + (size_t)(row0 + (int)((q + kPersistAhead) % nrow)) * nc),
-                                 "r"(bytes)
-                                 : "memory");
                 issued = q + 1;
             }
             // the copies in flight write this CTA's shared memory: let them land
@@ -424,17 +413,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             const int c0 = blockIdx.x * cpc, c1 = min(nc, c0 + cpc);
             for (int cb = c0; cb < c1; cb += 32) {
                 const int c = cb + lane;
-                // partials b = warp, warp + 8, ... of column c: all loads in flight
-                // before the (fixed-order) sum
-                float part[kPersistParts];
-#pragma unroll
-                for (int k = 0; k < kPersistParts; ++k) {
-                    const int b = warp + 8 * k;
-                    part[k] = (c < c1 && b < (int)gridDim.x) ? __ldcg(p.gpart + (size_t)b * nc + c) : 0.f;
-                }
                 float g = 0.f;
-#pragma unroll
-                for (int k = 0; k < kPersistParts; ++k) g += part[k];
+                if (c < c1)
+                    for (int b = warp; b < (int)gridDim.x; b += 8) g += __ldcg(p.gpart + (size_t)b * nc + c);
                 gred[warp][lane] = g;
                 bar_compute();
                 if (warp == 0 && c < c1) {
@@ -457,8 +438,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             ++nbar;
             bar_compute();
             if (stop_cta) break;
-            for (int i = 4 * tid; i < nc; i += 1024)      // n_cols % 4 == 0, x 16-byte aligned
-                *reinterpret_cast<float4 *>(xs + i) = __ldcg(reinterpret_cast<const float4 *>(p.x + i));
+            for (int i = tid; i < nc; i += 256) xs[i] = __ldcg(p.x + i);
             bar_compute();
         }
     }

@@ -230,6 +230,10 @@ cudaError_t dense_set_smem(size_t resid_bytes, size_t grad_bytes);
 cudaError_t dense_persist(const DenseParams &p, int iters, int grid, int S, size_t smem, int *err, unsigned int *gbar,
                           cudaStream_t s);
 cudaError_t dense_persist_set_smem(size_t bytes);
+// Tensor-core path (dense_tc.cu): device pointers; returns 0, -1 (no device) or
+// -2 (CUDA error); *herr receives a device error code (a bounded wait ran out).
+int dense_tc_nnls(int nr, int nc, int m, const float *B, const float *Y, int iters, float eta, float eps, float *X,
+                  float *G, double *loss, float *kernel_ms, int *herr, cudaStream_t st);
 cudaError_t launch_plain_build(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_route_choice(const PlainParams &p, cudaStream_t s);
 cudaError_t launch_plain_forward(const PlainParams &p, const float *q, float *xhat, cudaStream_t s);

@@ -96,3 +96,50 @@ def test_dense_one_pass_wait_runs_out_then_recovers():
     assert rel_norm(X, Xo, axis=0).max() < 1e-4
     with pytest.raises(dode.DodeError):
         dode.dense_set_wait_limit(-1)
+
+
+@pytest.mark.parametrize("nr,nc,m", [(512, 512, 16), (1000, 764, 64), (260, 1024, 256), (4, 36, 32)])
+def test_dense_tensor_cores_match_tf32_oracle(nr, nc, m):
+    """Many right-hand sides stacked into GEMMs on the tensor cores (method 3:
+    tcgen05 with TF32 operands and FP32 accumulation).  Against the oracle's
+    TF32 definition (the same operands, FP64 products and sums) the only
+    differences are FP32 accumulation and rounding, which can move an operand's
+    cut to TF32 by one TF32 unit (2^-10 relative) on a few elements: 1e-3
+    normwise on X and on the loss.  Against the FP64 oracle the TF32 operands
+    (relative error below 2^-10 each) move X by 4e-4 to 5e-4 normwise after 30
+    steps on the square and tall instances and by 1.2e-2 on the wide one (260
+    rows, 1024 columns: underdetermined, so the iterates are less constrained);
+    the bound is 2e-2.  Ragged M and K tiles (1000 rows, 764 columns) and the
+    largest tile (m = 256) included."""
+    from oracle.dense_nnls import spgd_dense_tf32
+    B, Y = _instance(nr, nc, m, seed=nr + 3 * nc + m)
+    X, G, loss, ms = dode.dense_nnls(B, Y, 30, 0.05, method=3)
+    Xt, _, lt = spgd_dense_tf32(B, Y, 30, 0.05)
+    Xo, _, lo = spgd_dense(B, Y, 30, 0.05)
+    e_t = rel_norm(X, Xt, axis=0).max()
+    e_o = rel_norm(X, Xo, axis=0).max()
+    print(f"tensor cores {nr}x{nc}, m={m}: X vs TF32 oracle {e_t:.2e}, vs FP64 oracle {e_o:.2e}, "
+          f"loss vs TF32 {np.max(np.abs(loss - lt) / lt):.2e}")
+    assert e_t < 1e-3
+    np.testing.assert_allclose(loss, lt, rtol=1e-3)
+    assert e_o < 2e-2
+    assert np.all(X >= 0) and ms > 0
+
+
+def test_dense_tensor_cores_device_pointers_and_limits():
+    torch = pytest.importorskip("torch")
+    B, Y = _instance(384, 512, 32, seed=17)
+    Xh, Gh, lh, _ = dode.dense_nnls(B, Y, 10, 0.05, method=3)
+    Bd, Yd = torch.from_numpy(B).cuda(), torch.from_numpy(Y).cuda()
+    Xd, Gd, ld, _ = dode.dense_nnls(Bd, Yd, 10, 0.05, method=3)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Xd.cpu().numpy(), Xh)
+    np.testing.assert_array_equal(ld.cpu().numpy(), lh)
+    # continuing from the returned state equals a longer run
+    X2, _, l2, _ = dode.dense_nnls(B, Y, 10, 0.05, X0=Xh, G0=Gh, method=3)
+    X20, _, l20, _ = dode.dense_nnls(B, Y, 20, 0.05, method=3)
+    np.testing.assert_array_equal(X2, X20)
+    for bad_m in (8, 24):                                         # m must be a multiple of 16
+        with pytest.raises(dode.DodeError) as e:
+            dode.dense_nnls(B, np.zeros((384, bad_m), np.float32), 1, 0.05, method=3)
+        assert e.value.code == dode.ERR_UNSUPPORTED

@@ -690,3 +690,32 @@ def test_dense_spgd_pins():
     np.testing.assert_allclose(X[:, 0], xs, atol=1e-6)
     grad = Bw.T @ (Bw @ X[:, 0] - yn[:, 0])
     assert np.all(grad > -1e-6) and np.all(np.abs(grad[X[:, 0] > 1e-8]) < 1e-6)
+
+
+def test_tf32_operand_rule():
+    """The TF32 operand rule keeps exactly the top 19 bits of an FP32 value
+    (sign, exponent, 10 mantissa bits): values with at most 11 significant bits
+    pass unchanged, the next bit is dropped toward zero, and the result differs
+    from the input by less than 2^-10 relative."""
+    from oracle.dense_nnls import tf32
+    exact = np.array([1.0, -3.5, 1 + 2 ** -10, 2 ** -20, 1024.0 + 1.0, 0.0], np.float32)
+    np.testing.assert_array_equal(tf32(exact), exact)
+    np.testing.assert_array_equal(tf32(np.float32(1 + 2 ** -11)), np.float32(1.0))
+    np.testing.assert_array_equal(tf32(np.float32(-(1 + 2 ** -10 + 2 ** -11))), np.float32(-(1 + 2 ** -10)))
+    x = np.random.default_rng(0).standard_normal(10000).astype(np.float32)
+    t = tf32(x)
+    assert np.all(np.abs(t) <= np.abs(x)) and np.all(np.abs(t - x) < 2.0 ** -10 * np.abs(x))
+
+
+def test_tf32_dense_oracle_reduces_to_fp64_on_tf32_exact_inputs():
+    """With B, Y and every iterate exactly representable in TF32 the TF32
+    definition is the FP64 one up to FP32 storage: a small instance whose
+    entries are multiples of 1/8 in [-2, 2]."""
+    from oracle.dense_nnls import spgd_dense, spgd_dense_tf32
+    rng = np.random.default_rng(4)
+    B = (rng.integers(-16, 17, (6, 5)) / 8.0).astype(np.float32)
+    Y = (B.astype(np.float64) @ np.abs(rng.integers(0, 4, (5, 2)) / 4.0)).astype(np.float32)
+    X64, _, l64 = spgd_dense(B, Y, 1, 0.25)
+    X32, _, l32 = spgd_dense_tf32(B, Y, 1, 0.25)
+    # one step from X = 0: R = -Y and g = -B^T Y are exact in TF32 here
+    np.testing.assert_allclose(X32, X64, rtol=1e-6)
