@@ -14,7 +14,7 @@
 //
 // Work items are (128-row M tile, range of K tiles): when there are fewer M tiles
 // than SMs the K dimension is split.  Each item writes its partial product; a
-// second kernel (k_tc_reduce, one block per M tile and 32 columns) sums the
+// second kernel (k_tc_reduce, one block per M tile and 8 columns) sums the
 // partials in K-range order and applies the epilogue, so results do not depend
 // on timing.  Each item walks its K tiles from a rotated start, so that the CTAs
 // do not all read the same Bop tile from L2 at the same time.
@@ -44,6 +44,7 @@ constexpr int kTcM = 128;                 // rows per tile (TMEM lanes)
 constexpr int kTcK = 32;                  // K per tile: 32 FP32 = one 128-byte swizzle row
 constexpr int kTcStages = 4;              // ring stages at most (fewer when they do not fit in shared memory)
 constexpr int kTcThreads = 256;
+constexpr int kTcRedCols = 8;             // columns per block of the reduce-and-epilogue kernel
 constexpr long long kTcWait = 1ll << 26;
 
 enum TcEpi : int { TC_RESID = 0, TC_STEP = 1 };
@@ -282,16 +283,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // The split-K partials of C summed in K-range order, then the epilogue: block
-// (M tile, 32 columns), thread = row of the tile.
+// (M tile, kTcRedCols columns), thread = row of the tile; narrow column blocks
+// give enough blocks to hide the partials' load latency.
 //   TC_RESID: Rt[j][i] = C[i][j] - Y[i][j]; lpart[tile][j] = sum over the tile's rows of r^2
 //   TC_STEP:  Gt[j][i] += g^2, Xt[j][i] = max(Xt[j][i] - eta g / (sqrt(Gt) + eps), 0) with g = C[i][j]
 template <int EPI>
 __global__ void __launch_bounds__(kTcM) k_tc_reduce(const TcParams p) {
-    __shared__ double red[4][32];
-    const int tile = blockIdx.x, j0 = blockIdx.y * 32, r = threadIdx.x, lane = r & 31, w = r >> 5;
+    __shared__ double red[4][kTcRedCols];
+    const int tile = blockIdx.x, j0 = blockIdx.y * kTcRedCols, r = threadIdx.x, lane = r & 31, w = r >> 5;
     const int row = tile * kTcM + r;
     const bool live = row < p.M;
-    const int nj = min(32, p.N - j0);
+    const int nj = min(kTcRedCols, p.N - j0);
     for (int jq = 0; jq < nj; jq += 8) {
         float c[8];
 #pragma unroll
@@ -409,7 +411,7 @@ static cudaError_t tc_launch(const CUtensorMap &a, const CUtensorMap &b, const T
     k_tc_gemm<<<grid, kTcThreads, tc_smem(p.N), s>>>(a, b, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_tc_reduce<EPI><<<dim3(p.m_tiles, (p.N + 31) / 32), kTcM, 0, s>>>(p);
+    k_tc_reduce<EPI><<<dim3(p.m_tiles, (p.N + kTcRedCols - 1) / kTcRedCols), kTcM, 0, s>>>(p);
     return cudaGetLastError();
 }
 
