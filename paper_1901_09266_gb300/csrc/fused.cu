@@ -406,7 +406,13 @@ __device__ __forceinline__ void group_flows(const FusedParams &p, const Shared &
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (t0 + u < m) {
-                const long long fu = __float2ll_rn(pv[u] * qv[u] * kFxScale);
+                // 32-bit conversion whenever the flow fits (the 64-bit one runs on the slow FP64 pipe)
+                const float x = pv[u] * qv[u] * kFxScale;
+                long long fu;
+                if (x >= 0.f && x < 2147483520.f)
+                    fu = __float2int_rn(x);
+                else
+                    fu = __float2ll_rn(x);
                 nonneg = nonneg && fu >= 0;
                 any = any || fu != 0;
                 acc += fu;
@@ -540,7 +546,9 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
 
 // Route flows of both tiles of a pair task: exclusive prefix sums interleaved
 // per route (x: tile A, y: tile B), so that one 8-byte local access serves both
-// chains; 32 bits suffice for the integer form the pair walk takes (fast).
+// chains; 32 bits suffice for the integer form the pair walk takes (fast).  A
+// flow outside [0, 2^31) units (or not a number) makes the task not fast; it is
+// then walked as two single tiles, which convert in 64 bits.
 template <int PREC>
 __device__ __forceinline__ void group_flows2(const FusedParams &p, const Shared &s, int day, int i0, int m, int bA,
                                              int bB, bool vwA, bool vwB, uint2 *S, bool &any, bool &fast) {
@@ -570,10 +578,14 @@ __device__ __forceinline__ void group_flows2(const FusedParams &p, const Shared 
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (t0 + u < m) {
-                const long long fa = __float2ll_rn(pa[u] * qa[u] * kFxScale);
-                const long long fb = __float2ll_rn(pb[u] * qb[u] * kFxScale);
-                nonneg = nonneg && fa >= 0 && fb >= 0;
-                any = any || fa != 0 || fb != 0;
+                // the pair walk needs every flow in [0, 2^31) units: a 32-bit
+                // conversion then gives the same integer as a 64-bit one, and keeps
+                // the slow FP64 pipe (which takes 64-bit conversions) free
+                const float xa = pa[u] * qa[u] * kFxScale, xb = pb[u] * qb[u] * kFxScale;
+                const bool in = xa >= 0.f && xa < 2147483520.f && xb >= 0.f && xb < 2147483520.f;
+                const int fa = in ? __float2int_rn(xa) : 0, fb = in ? __float2int_rn(xb) : 0;
+                nonneg = nonneg && in;
+                any = any || fa != 0 || fb != 0 || !in;     // out of range: the single-tile walks decide
                 accA += fa;
                 accB += fb;
                 S[t0 + u + 1] = make_uint2((uint32_t)accA, (uint32_t)accB);
