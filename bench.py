@@ -486,6 +486,7 @@ def run_gpu(args):
                 pt_["graph" if graph else "direct"] = {
                     "day_iter_per_s": n * args.uneven_epochs / t, "call_ms": t * 1e3,
                     "kernel_ms": cu.last_kernel_ms(), "grid": cu.last_grid(),
+                    "epoch_slices": cu.last_slices(),
                     "shape": {k: tuned_u[k] for k in ("block", "ctas_per_sm", "max_ctas")},
                     "final_loss": float(ln.double().sum().item())}
                 cu.close()
@@ -642,7 +643,7 @@ def run_gpu(args):
             "config": {"workload": w.name, "days_per_gpu": D, "intervals": N, "od_pairs": K,
                        "routes": w.routes.n_routes, "links": A, "detectors": O, "epochs_per_step": E,
                        "form": args.form, "precision": args.precision, "graph": bool(args.graph),
-                       "row_chunk": args.row_chunk,
+                       "row_chunk": args.row_chunk, "epoch_slices": ctx.last_slices(),
                        "launch": tuned or {"block": args.block, "ctas_per_sm": args.ctas},
                        "l2": "inputs larger than L2 (reloaded every step)"},
             "e2e": {"value": e2e_value, "unit": "day-iter/s", "h2d_bytes_per_step": int(h2d),

@@ -126,6 +126,13 @@ typedef struct {
                                 Each epoch then takes two launches; use_graph is ignored.
                                 dode_dar_distance, dode_get_dar and dode_loss_static_scratch
                                 refuse coupled days.  0 = independent days (default). */
+    int32_t epoch_slices;    /* fused solve of independent days: cut each day's epochs into this many
+                                slices, handed out slice-major so that no CTA idles while the last
+                                days run (slice s of a day starts when its slice s - 1 is done; a
+                                wait past 20 s gives DODE_ERR_DEVICE_TIMEOUT).  Results are
+                                bitwise the same for any value.  0 = automatic (min(16, iters / 4)
+                                slices when there are at least twice as many days as CTAs and
+                                iters >= 8, else 1); 1 = whole days. */
 } dode_options;
 
 typedef struct dode_ctx dode_ctx;
@@ -369,6 +376,10 @@ double dode_last_kernel_ms(const dode_ctx *ctx);
 int64_t dode_last_launches(const dode_ctx *ctx);
 /* CTAs of the last call's fused-kernel launch (0 if that call ran no fused kernel). */
 int32_t dode_last_grid(const dode_ctx *ctx);
+
+/* Epoch slices per day of the last fused solve (1 = whole days; see
+ * dode_options.epoch_slices); 0 before any fused solve.                      */
+int32_t dode_last_slices(const dode_ctx *ctx);
 /* CUDA device ordinal the context runs on (-1 for a NULL context). */
 int32_t dode_device(const dode_ctx *ctx);
 /* Number of kernel launches (all kernels, all calls) made by this context so far. */

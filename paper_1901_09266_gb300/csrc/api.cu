@@ -73,6 +73,8 @@ struct dode_ctx {
     float *d_q = nullptr, *d_G = nullptr, *d_qtmp = nullptr, *d_gout = nullptr, *d_xout = nullptr;
     __nv_bfloat16 *d_qb = nullptr;
     double *d_loss = nullptr, *d_dtheta = nullptr;
+    int *d_progress = nullptr;   // [D] epoch slices done per day (fused solve with slices)
+    int last_slices = 0;
     double *d_totals = nullptr;  // [2] cross-day totals (dode_last_totals)
     int totals_kind = 0;         // what d_loss / d_dtheta hold: 0 nothing, 1 losses, 2 losses and dL/dtheta
     float *d_trace = nullptr;
@@ -106,6 +108,7 @@ struct dode_ctx {
     int64_t total_launches = 0;
     // CUDA graph of dode_solve's device work (use_graph)
     cudaGraphExec_t graph_exec = nullptr;
+    int graph_slices = 1;                  // epoch slices of the captured solve
     cudaStream_t own_stream = nullptr;     // capture stream when the context uses the legacy default stream
     struct GraphKey {
         int iters = -1, grid = 0, block = 0, ring = 0, tick = 0, F = 0, prec = -1;
@@ -592,7 +595,20 @@ FusedParams base_params(dode_ctx *ctx) {
     p.early = ctx->d_early;
     p.halo = ctx->d_halo;
     p.no_final = 0;
+    p.slices = 1;
+    p.progress = nullptr;
+    p.wait_ns = 20000000000LL;
     return p;
+}
+
+// Epoch slices of a fused solve over `grid` CTAs (see dode_options.epoch_slices):
+// worth it once the days outnumber the CTAs twice, so that a day's next slice
+// sits D units after its last in the queue and is rarely waited for.
+int choose_slices(const dode_ctx *ctx, const FusedParams &p, int grid) {
+    if (p.mode != MODE_SOLVE || p.coupled || p.iters < 2 || !ctx->d_progress) return 1;
+    if (ctx->opt.epoch_slices > 0) return std::min(ctx->opt.epoch_slices, p.iters);
+    if (p.iters < 8 || ctx->D < 2 * grid) return 1;
+    return std::min(16, p.iters / 4);
 }
 
 int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
@@ -614,6 +630,12 @@ int run_fused(dode_ctx *ctx, FusedParams p, int precision) {
         CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
         CUL(launch_fused(ph, precision, s.grid, s.block, s.smem, ctx->stream));
         ++ctx->last_launches;
+    }
+    p.slices = choose_slices(ctx, p, s.grid);
+    ctx->last_slices = p.mode == MODE_SOLVE ? p.slices : ctx->last_slices;
+    if (p.slices > 1) {
+        p.progress = ctx->d_progress;
+        CU(cudaMemsetAsync(ctx->d_progress, 0, (size_t)ctx->D * sizeof(int), ctx->stream));
     }
     CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), ctx->stream));
     CUL(launch_fused(p, precision, s.grid, s.block, s.smem, ctx->stream));
@@ -693,6 +715,7 @@ void free_days(dode_ctx *ctx) {
     dfree(ctx->d_xout);
     dfree(ctx->d_loss);
     dfree(ctx->d_dtheta);
+    dfree(ctx->d_progress);
     dfree(ctx->d_early);
     dfree(ctx->d_halo);
     ctx->halo_rows = 0;
@@ -782,6 +805,9 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
     if (!ctx->graph_exec || !(key == ctx->graph_key)) {
         drop_graph(ctx);
         slot_params(ctx, s, &p);
+        p.slices = choose_slices(ctx, p, s.grid);
+        if (p.slices > 1) p.progress = ctx->d_progress;
+        ctx->graph_slices = p.slices;
         CU(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         const int D = ctx->D;
@@ -791,6 +817,8 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
             e = launch_route_choice(choice_C(ctx), ctx->d_rod, ctx->d_od_ptr, ctx->d_od_routes, p.theta, D, ctx->P,
                                     ctx->N, ctx->Np, ctx->d_pt, gs);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_queue, 0, sizeof(int), gs);
+        if (e == cudaSuccess && p.slices > 1)
+            e = cudaMemsetAsync(ctx->d_progress, 0, (size_t)D * sizeof(int), gs);
         // external event-record nodes: the events complete with each replay, so
         // the kernel timer works for graph launches too
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->ev0, gs, cudaEventRecordExternal);
@@ -817,6 +845,7 @@ int solve_graph(dode_ctx *ctx, FusedParams p, int iters, float step, float *q_ou
     if (gs != ctx->stream) CU(cudaStreamSynchronize(gs));
     ctx->last_launches = 1;
     ctx->last_grid = s.grid;
+    ctx->last_slices = ctx->graph_slices;
     ctx->total_launches += kernels;
     return DODE_OK;
 }
@@ -860,6 +889,8 @@ int64_t dode_last_launches(const dode_ctx *ctx) { return ctx ? ctx->last_launche
 
 int32_t dode_last_grid(const dode_ctx *ctx) { return ctx ? ctx->last_grid : 0; }
 
+int32_t dode_last_slices(const dode_ctx *ctx) { return ctx ? ctx->last_slices : 0; }
+
 int32_t dode_device(const dode_ctx *ctx) { return ctx ? ctx->dev : -1; }
 
 int64_t dode_total_launches(const dode_ctx *ctx) { return ctx ? ctx->total_launches : 0; }
@@ -890,7 +921,7 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
         !(o.eps >= 0.f) || o.row_chunk < 0 || (o.form != DODE_FORM_FUSED && o.form != DODE_FORM_PLAIN) ||
         (o.precision != DODE_PREC_FP32 && o.precision != DODE_PREC_BF16) || o.block_threads < 0 || o.ctas_per_sm < 0 ||
         o.max_ctas < 0 || (o.use_graph != 0 && o.use_graph != 1) || o.day_base < 0 ||
-        (o.couple_days != 0 && o.couple_days != 1))
+        (o.couple_days != 0 && o.couple_days != 1) || o.epoch_slices < 0)
         return bail(DODE_ERR_ARG, "options");
     if (o.couple_days && (o.form != DODE_FORM_FUSED || o.row_chunk > 0))
         return bail(DODE_ERR_ARG, "couple_days needs the fused form with full-row updates (row_chunk = 0)");
@@ -1125,6 +1156,7 @@ int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const floa
         CU(dalloc(&ctx->d_qtmp, (size_t)D * ctx->K * Np));
         CU(dalloc(&ctx->d_loss, (size_t)D));
         CU(dalloc(&ctx->d_dtheta, (size_t)D));
+        CU(dalloc(&ctx->d_progress, (size_t)D));
         ctx->D = D;
     }
     ctx->plain_ready = false;

@@ -134,6 +134,11 @@ struct FusedParams {
     long long *early;          // [D][O][S] own deposits into the day's rows [0, S), 2^-20 vehicles
     long long *halo;           // [D][O][S] deposits into the next day's rows [0, S)
     int no_final;              // SOLVE: stop after the last step, no final forward
+    // epoch slices (SOLVE): work unit u is slice u / D of day u % D, epochs
+    // [s iters / S, (s + 1) iters / S); slice s of a day waits until slice s - 1 is done
+    int slices;                // S >= 1
+    int *progress;             // [D] slices done per day (zero at launch), or null when S = 1
+    long long wait_ns;         // bound on that wait (globaltimer ns); past it: kErrDeviceTimeout
 };
 
 struct PrepParams {

@@ -1516,6 +1516,42 @@ __device__ __forceinline__ TaskRef task_ref(int t, int nt, int nb, int pb0, cons
 // Dynamic shared memory layout (16-byte aligned blocks):
 //   groute int4[P] | gptr int[G+1] | task_grp int[G] |
 //   OD tables int[G+1 + n_god + n_god+1 + n_godr] | colact u32[Ow] | lo u32[O][R] | tw u16[A][RW]
+// Epoch slices.  The epochs of one day are a chain (each reads the demand and
+// Adagrad state the one before wrote), so with one CTA per day the last round
+// of days leaves most CTAs idle.  Cutting each day's epochs into S slices and
+// handing out (slice, day) units slice-major keeps every CTA busy to within one
+// slice: a day's slice s follows its slice s - 1 by D units in the queue.  The
+// CTA that finishes a slice publishes it with a release store after its
+// writes; the CTA that takes the next slice waits (bounded) for it with an
+// acquire load.  A unit waits only on a unit taken earlier by a running CTA,
+// so the waits always end.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int load_acquire(const int *a) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void store_release(int *a, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// Thread 0: wait until day's slice count reaches `need`; false after wait_ns.
+__device__ bool wait_slice(const FusedParams &p, int day, int need) {
+    if (load_acquire(&p.progress[day]) >= need) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        __nanosleep(256);
+        if (load_acquire(&p.progress[day]) >= need) return true;
+        if ((long long)(global_ns() - t0) > p.wait_ns) return false;
+    }
+}
+
 template <int PREC, bool SMEM_RING, bool SMEM_TICKS>
 __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1550,6 +1586,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     s.rtab32 = (p.rtab_off >= 0 && p.rtab_packed) ? reinterpret_cast<const uint32_t *>(smem_raw + p.rtab_off) : nullptr;
     s.hi = SMEM_RING ? reinterpret_cast<int *>(p.gring) + (size_t)blockIdx.x * p.O * s.R : nullptr;
     __shared__ int s_day;
+    __shared__ int s_slice;
     __shared__ int s_task;
     __shared__ double s_red[32];
     __shared__ double s_dth;
@@ -1597,10 +1634,25 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
 
     while (true) {
         __syncthreads();
-        if (threadIdx.x == 0) s_day = atomicAdd(p.queue, 1);
+        if (threadIdx.x == 0) {
+            const int u = atomicAdd(p.queue, 1);
+            const int sl = u / p.n_days, d = u - sl * p.n_days;
+            int code = d;
+            if (sl >= p.slices)
+                code = -1;                                 // no work left
+            else if (sl > 0 && !wait_slice(p, d, sl)) {
+                set_error(p.err, kErrDeviceTimeout, d);
+                code = -1;
+            }
+            s_day = code;
+            s_slice = sl;
+        }
         __syncthreads();
         const int day = s_day;
-        if (day >= p.n_days) break;
+        if (day < 0) break;
+        const int slice = s_slice;
+        const int it_begin = (int)((long long)slice * p.iters / p.slices);
+        const int it_end = (int)((long long)(slice + 1) * p.iters / p.slices);
         const bool has_next = p.coupled && day + 1 < p.n_days;
         // a coupled day also deposits on the next day's observed links (its trips
         // that cross midnight)
@@ -1639,7 +1691,7 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
         const bool chunked = p.mode == MODE_SOLVE && p.row_chunk > 0;
         const int32_t *lab = chunked ? p.lab + (size_t)blockIdx.x * p.O * p.Np : nullptr;
         int nch = 1;
-        for (int it = 0, chunk = 0;;) {
+        for (int it = it_begin, chunk = 0;;) {
             if (chunked && it < p.iters && chunk == 0) nch = row_labels(p, mk, p.day_base + day, it, &s_nrows);
             const int sel = (chunked && it < p.iters) ? chunk : -1;     // chunk of rows in this update
             // ------------------------------ forward sweep ------------------------------
@@ -1854,6 +1906,14 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
             chunk = 0;
             ++it;
             if (p.no_final && it >= p.iters) break;        // the caller takes the final loss
+            if (it >= it_end && it_end < p.iters) break;   // the slice's epochs are done
+        }
+        if (p.slices > 1) {
+            __syncthreads();                               // the slice's writes of q and G ...
+            if (threadIdx.x == 0) {
+                __threadfence();
+                store_release(&p.progress[day], slice + 1);   // ... before its count
+            }
         }
     }
 }

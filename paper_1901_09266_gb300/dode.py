@@ -31,7 +31,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
            "dode_loss_grad", "dode_last_totals", "dode_dense_nnls", "dode_dense_set_wait_limit", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
-           "dode_last_kernel_ms", "dode_last_launches", "dode_last_grid", "dode_total_launches", "dode_device", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
+           "dode_last_kernel_ms", "dode_last_launches", "dode_last_grid", "dode_last_slices", "dode_total_launches", "dode_device", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
 
@@ -62,7 +62,8 @@ class dode_options(ct.Structure):
                 ("seed", ct.c_uint64), ("form", ct.c_int32), ("precision", ct.c_int32),
                 ("block_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32), ("device", ct.c_int32),
                 ("stream", ct.c_void_p), ("use_graph", ct.c_int32), ("max_ctas", ct.c_int32),
-                ("day_base", ct.c_int32), ("couple_days", ct.c_int32)]
+                ("day_base", ct.c_int32), ("couple_days", ct.c_int32),
+                ("epoch_slices", ct.c_int32)]
 
 
 _lib = None
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
         "dode_last_kernel_ms": (f64, [vp]),
         "dode_last_launches": (i64, [vp]),
         "dode_last_grid": (i32, [vp]),
+        "dode_last_slices": (i32, [vp]),
         "dode_device": (i32, [vp]),
         "dode_total_launches": (i64, [vp]),
         "dode_set_launch": (ct.c_int, [vp, i32, i32]),
@@ -399,6 +401,10 @@ class Context:
     def last_grid(self) -> int:
         """``dode_last_grid``: CTAs of the last call's fused-kernel launch."""
         return int(load().dode_last_grid(self.h))
+
+    def last_slices(self) -> int:
+        """``dode_last_slices``: epoch slices per day of the last fused solve (1 = whole days)."""
+        return int(load().dode_last_slices(self.h))
 
     def total_launches(self) -> int:
         """``dode_total_launches``: all kernel launches of this context."""
