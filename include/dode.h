@@ -131,8 +131,8 @@ typedef struct {
                                 days run (slice s of a day starts when its slice s - 1 is done; a
                                 wait past 20 s gives DODE_ERR_DEVICE_TIMEOUT).  Results are
                                 bitwise the same for any value.  0 = automatic (min(16, iters / 4)
-                                slices when there are at least twice as many days as CTAs and
-                                iters >= 8, else 1); 1 = whole days. */
+                                slices when there are more days than CTAs and iters >= 8, else 1);
+                                1 = whole days. */
 } dode_options;
 
 typedef struct dode_ctx dode_ctx;

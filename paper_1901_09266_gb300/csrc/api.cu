@@ -602,12 +602,13 @@ FusedParams base_params(dode_ctx *ctx) {
 }
 
 // Epoch slices of a fused solve over `grid` CTAs (see dode_options.epoch_slices):
-// worth it once the days outnumber the CTAs twice, so that a day's next slice
-// sits D units after its last in the queue and is rarely waited for.
+// worth it once the days outnumber the CTAs (whole days would leave a partial
+// last round); a day's next slice sits D > grid units after its last in the
+// queue, about one slice's time later, so it is rarely waited for long.
 int choose_slices(const dode_ctx *ctx, const FusedParams &p, int grid) {
     if (p.mode != MODE_SOLVE || p.coupled || p.iters < 2 || !ctx->d_progress) return 1;
     if (ctx->opt.epoch_slices > 0) return std::min(ctx->opt.epoch_slices, p.iters);
-    if (p.iters < 8 || ctx->D < 2 * grid) return 1;
+    if (p.iters < 8 || ctx->D <= grid) return 1;
     return std::min(16, p.iters / 4);
 }
 

@@ -14,7 +14,7 @@ from tests.helpers import inputs, rel_norm
 pytestmark = pytest.mark.gpu
 
 D = 80
-CTAS = 16          # D >= 2 x CTAs: the automatic choice slices the days
+CTAS = 16          # more days than CTAs: the automatic choice slices the days
 EPOCHS = 12
 
 
@@ -69,12 +69,19 @@ def test_sliced_solve_matches_oracle_on_sampled_days(days80):
 
 def test_automatic_choice_keeps_whole_days_when_few(days80):
     w, net, sp, counts, mask = days80
-    # fewer epochs than the automatic rule slices, and fewer days than twice the CTAs
+    # fewer epochs than the automatic rule slices, and no more days than CTAs
     assert _solve(w, sp, counts, mask, 0, iters=6)[3] == 1
-    ctx = dode.Context.from_workload(w, max_ctas=64)
+    ctx = dode.Context.from_workload(w, max_ctas=D)
     ctx.set_days(counts, sp, mask)
     ctx.solve(EPOCHS, 5.0)
-    assert ctx.last_grid() == 64 and ctx.last_slices() == 1
+    assert ctx.last_grid() == D and ctx.last_slices() == 1
+    ctx = dode.Context.from_workload(w, max_ctas=D - 1)    # one day more than CTAs: sliced
+    ctx.set_days(counts, sp, mask)
+    q, loss = ctx.solve(EPOCHS, 5.0)
+    assert ctx.last_grid() == D - 1 and ctx.last_slices() == EPOCHS // 4
+    q1, l1, _, _ = _solve(w, sp, counts, mask, 1)
+    np.testing.assert_array_equal(q, q1)
+    np.testing.assert_array_equal(loss, l1)
 
 
 def test_sliced_graph_replay_bitwise_equal(days80):
