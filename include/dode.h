@@ -57,6 +57,9 @@ extern "C" {
 #define DODE_ERR_DEVICE_TIMEOUT -8       /* a bounded device wait gave up */
 #define DODE_ERR_STATE -9                /* call order: e.g. solve before set_days */
 #define DODE_ERR_UNSUPPORTED -10         /* valid input this form does not handle */
+#define DODE_ERR_BOUNDS -11              /* debug build only (-DDODE_CHECK_BOUNDS): a device index check
+                                            failed; dode_last_error names the site and the index, and
+                                            the access was skipped */
 
 /* ---- enums ------------------------------------------------------------------ */
 #define DODE_PTR_HOST 0

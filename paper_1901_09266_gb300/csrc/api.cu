@@ -205,6 +205,10 @@ int check_device_error(dode_ctx *ctx) {
         snprintf(buf, sizeof buf, "%s at day %lld, interval %lld, link %lld",
                  h[0] == DODE_ERR_BAD_SPEED ? "speed not finite and positive" : "link travel time above 2^24 ticks",
                  dh / ctx->N, dh % ctx->N, a);
+    } else if (h[0] == DODE_ERR_BOUNDS) {
+        long long i = idx & ((1ll << 40) - 1);
+        if (i >= (1ll << 39)) i -= 1ll << 40;
+        snprintf(buf, sizeof buf, "index check failed at site %lld: index %lld", idx >> 40, i);
     } else if (h[0] == DODE_ERR_UNSUPPORTED) {
         snprintf(buf, sizeof buf, "unsupported input at item %lld (window spans more intervals than this form handles)", idx);
     } else {

@@ -197,6 +197,7 @@ __global__ void k_dense_loss(const double *__restrict__ lpart, int n_part, int m
 // ---------------------------------------------------------------------------
 constexpr int kPersistStages = 8;                   // ring stages (rows): 4 or 8, a multiple of the residual warps
 constexpr int kPersistStrips = 16;                  // n_cols <= 16 * 512
+constexpr int kReloadVecs = kPersistStrips * 512 / 4 / 256;   // 16-byte loads per compute thread for x
 constexpr int kPersistThreads = 288;                // 8 compute warps + 1 producer warp
 constexpr long long kDrainLimit = 1ll << 26;
 
@@ -293,6 +294,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 if (abort_cta) break;
                 const uint32_t bytes = (uint32_t)nc * 4u;
                 float *dst = ring + (size_t)st * nc;
+                if (!DODE_IN_BOUNDS(row0 + (int)(q % nrow), nr, err, kSiteDenseRing)) {
+                    abort_cta = 1;
+                    break;
+                }
                 const float *src = p.B + (size_t)(row0 + (int)(q % nrow)) * nc;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
@@ -415,7 +420,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 const int c = cb + lane;
                 float g = 0.f;
                 if (c < c1)
-                    for (int b = warp; b < (int)gridDim.x; b += 8) g += __ldcg(p.gpart + (size_t)b * nc + c);
+                    for (int b = warp; b < (int)gridDim.x; b += 8)
+                        if (DODE_IN_BOUNDS((long long)b * nc + c, (long long)gridDim.x * nc, err, kSiteDensePart))
+                            g += __ldcg(p.gpart + (size_t)b * nc + c);
                 gred[warp][lane] = g;
                 bar_compute();
                 if (warp == 0 && c < c1) {
@@ -438,7 +445,21 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             ++nbar;
             bar_compute();
             if (stop_cta) break;
-            for (int i = tid; i < nc; i += 256) xs[i] = __ldcg(p.x + i);
+            {
+                // all of x in one round trip: n_cols <= 8192, 16-byte loads
+                const int n4 = nc >> 2;
+                float4 xv[kReloadVecs];
+#pragma unroll
+                for (int u = 0; u < kReloadVecs; ++u) {
+                    const int i = tid + 256 * u;
+                    xv[u] = i < n4 ? __ldcg(reinterpret_cast<const float4 *>(p.x) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < kReloadVecs; ++u) {
+                    const int i = tid + 256 * u;
+                    if (i < n4) reinterpret_cast<float4 *>(xs)[i] = xv[u];
+                }
+            }
             bar_compute();
         }
     }

@@ -31,7 +31,8 @@ constexpr int kRankBins = 4096;       // row-chunk ranking: bins on the keys' to
 // into its first halo_rows rows (early) and its deposits past midnight (halo).
 enum Mode : int { MODE_SOLVE = 0, MODE_FORWARD = 1, MODE_LOSS = 2, MODE_LOSS_GRAD = 3, MODE_HALO = 4 };
 
-// floor(t / ipt) for 0 <= t < 2^31 via a 32-bit magic multiplier:
+// floor(t / ipt) for 0 <= t < 2^31 via a 32-bit magic multiplier (division by
+// an invariant integer using multiplication, Granlund and Montgomery, 1994):
 // with l = ceil(log2 ipt) and M = ceil(2^(31+l) / ipt) < 2^32,
 // floor(t / ipt) = umulhi(t, M) >> (l - 1) for every t < 2^31.
 struct IntervalDiv {
@@ -196,7 +197,8 @@ struct DenseParams {
 };
 
 // error codes mirrored from dode.h for device use
-constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrDeviceTimeout = -8, kErrUnsupported = -10;
+constexpr int kErrArg = -1, kErrBadSpeed = -4, kErrTickOverflow = -5, kErrDeviceTimeout = -8, kErrUnsupported = -10,
+              kErrBounds = -11;
 
 __device__ __forceinline__ void set_error(int *err, int code, long long index) {
     if (atomicCAS(err, 0, code) == 0) {
@@ -204,6 +206,37 @@ __device__ __forceinline__ void set_error(int *err, int code, long long index) {
         err[2] = (int)(index >> 31);
     }
 }
+
+// Index checks of the debug build (compiled with -DDODE_CHECK_BOUNDS): before a
+// checked access, DODE_IN_BOUNDS(i, n, err, site) tests 0 <= i < n; a failed
+// test records kErrBounds with the site number (bits 40..) and the low 40 bits
+// of the index in the error word and the access is skipped, so a bad index
+// never reaches memory.  The normal build compiles every check to `true`.
+enum BoundsSite : int {
+    kSiteRingDeposit = 1,     // accumulator cell of a deposit (shared ring or global)
+    kSiteTickWindow = 2,      // tick read by a walk (shared window or global table)
+    kSiteRingGather = 3,      // residual cell read by an adjoint walk
+    kSiteWalkStack = 4,       // depth of a walk's branch-point stack
+    kSiteGroupSums = 5,       // route index of a group's prefix sums
+    kSiteFlushCell = 6,       // ring cell of a flush or a spill move
+    kSiteStageTicks = 7,      // tick window row staged into shared memory
+    kSiteStageResid = 8,      // residual window cell staged into shared memory
+    kSiteDemand = 9,          // (day, OD, departure) cell of q and G
+    kSiteDenseRing = 10,      // row copy of the dense one-pass ring
+    kSiteDensePart = 11,      // gradient partial of the dense one-pass step
+};
+
+__device__ __forceinline__ bool bounds_check(long long i, long long n, int *err, int site) {
+    if (i >= 0 && i < n) return true;
+    set_error(err, kErrBounds, ((long long)site << 40) | (i & ((1ll << 40) - 1)));
+    return false;
+}
+
+#ifdef DODE_CHECK_BOUNDS
+#define DODE_IN_BOUNDS(i, n, err, site) ::dode::bounds_check((long long)(i), (long long)(n), (err), (site))
+#else
+#define DODE_IN_BOUNDS(i, n, err, site) true
+#endif
 
 // launchers (defined in the .cu files)
 cudaError_t launch_ticks(const float *speeds, const float *len, int D, int N, int Np, int A, int tps,

@@ -111,6 +111,9 @@ struct Shared {
     const uint32_t *rtab32;  // [L] its 32-bit form in shared memory, or null
     int *carry;           // set once any deposit of this CTA carried into a high word
     int R, RW, pb;
+    int *err;             // error word (index checks of the debug build)
+    int ring_cells;       // accumulator / residual cells: O R (shared ring) or O Np (global)
+    int tick_cells;       // tick cells: A RW (shared window) or A Np (global table)
 };
 
 // Route links in registers: lane j holds, for position j (and j + 32) of the
@@ -177,6 +180,7 @@ __device__ __forceinline__ float first_share(int T, int e0, float inv) {
 // FAST: the caller guarantees 0 <= v < 3000 (then v 2^20 fits 32 unsigned bits).
 template <bool SMEM_RING, bool FAST = false>
 __device__ __forceinline__ void deposit(const Shared &s, float *gacc, int idx, float v) {
+    if (!DODE_IN_BOUNDS(idx, s.ring_cells, s.err, kSiteRingDeposit)) return;
     if (!SMEM_RING) {
         atomicAdd(gacc + idx, v);
         return;
@@ -218,7 +222,7 @@ __device__ __noinline__ float window_tail(const Shared &s, float *gacc, const vo
         }
         if (DEPOSIT)
             deposit<SMEM_RING>(s, gacc, idx, f * share);
-        else
+        else if (DODE_IN_BOUNDS(idx, s.ring_cells, s.err, kSiteRingGather))
             acc += share * (SMEM_RING ? __uint_as_float(s.lo[idx]) : Operand<PREC>::r(rb, (size_t)idx));
         ++idx;
         e += ipt;
@@ -230,6 +234,7 @@ __device__ __noinline__ float window_tail(const Shared &s, float *gacc, const vo
 // Add u units of 2^-20 vehicles (u < 2^32) to cell idx.
 template <bool SMEM_RING>
 __device__ __forceinline__ void deposit_u(const Shared &s, float *gacc, int idx, uint32_t u) {
+    if (!DODE_IN_BOUNDS(idx, s.ring_cells, s.err, kSiteRingDeposit)) return;
     if (!SMEM_RING) {
         atomicAdd(gacc + idx, (float)((double)u * kFxInv));
         return;
@@ -263,12 +268,22 @@ __device__ __noinline__ void window_tail_u(const Shared &s, float *gacc, int idx
     }
 }
 
+// Residual cell idx read by an adjoint walk: the shared window, or the CTA's
+// residual slot when the ring is global.
+template <int PREC, bool SMEM_RING>
+__device__ __forceinline__ float rcell(const Shared &s, const float *racc, const void *rb, int idx) {
+    if (!DODE_IN_BOUNDS(idx, s.ring_cells, s.err, kSiteRingGather)) return 0.f;
+    return SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx);
+}
+
 template <bool SMEM_TICKS, bool TAB>
 __device__ __forceinline__ int next_entry(const FusedParams &p, const Shared &s, const int32_t *tick_day,
                                           const int32_t *trow, int j, int T, int tb, int h0) {
     if (TAB) return __ldg(&trow[(size_t)(j + 1) * (p.N + 1)]);
-    if (SMEM_TICKS) return T + s.tw[tb + h0];
-    return T + __ldg(&tick_day[tb + min(h0, p.N - 1)]);
+    const int ti = SMEM_TICKS ? tb + h0 : tb + min(h0, p.N - 1);
+    if (!DODE_IN_BOUNDS(ti, s.tick_cells, s.err, kSiteTickWindow)) return T;
+    if (SMEM_TICKS) return T + s.tw[ti];
+    return T + __ldg(&tick_day[ti]);
 }
 
 // Forward walk of route t of a group from depth j0: every window on an
@@ -289,6 +304,7 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
                                                int T, bool vw, const long long *S, int t, int E, int *stk) {
     const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
+    if (!DODE_IN_BOUNDS(E + 1, kGroupRoutes + 1, s.err, kSiteGroupSums)) E = t;
     uint32_t Wu = (uint32_t)(S[E + 1] - S[t]);
     float Wf = __uint2float_rn(Wu);
     for (int j = j0; j < beta; ++j) {
@@ -298,6 +314,7 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
         const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
         if ((ev >> 1) != E) {          // routes branch off: fewer of them share this window
             E = ev >> 1;
+            if (!DODE_IN_BOUNDS(E + 1, kGroupRoutes + 1, s.err, kSiteGroupSums)) E = t;
             Wu = (uint32_t)(S[E + 1] - S[t]);
             Wf = __uint2float_rn(Wu);
         }
@@ -330,7 +347,7 @@ __device__ __forceinline__ void forward_walk_u(const FusedParams &p, const Share
                 window_tail_u<PREC, SMEM_RING>(s, gacc, ob + h0 + 1, hi, e0, h0 + 1, N, ipt, inv, Wf, Wu - u0);
         }
         T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
-        if (ev & 1) stk[j + 1] = T;
+        if ((ev & 1) && DODE_IN_BOUNDS(j + 1, kMaxRouteLinks + 1, s.err, kSiteWalkStack)) stk[j + 1] = T;
     }
 }
 
@@ -341,6 +358,7 @@ __device__ __forceinline__ void forward_walk_f(const FusedParams &p, const Share
                                                const int32_t *trow, const RouteRegs &rr, float *gacc, int j0, int beta,
                                                int T, bool vw, const long long *S, int t, int E, int *stk) {
     const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
+    if (!DODE_IN_BOUNDS(E + 1, kGroupRoutes + 1, s.err, kSiteGroupSums)) E = t;
     float f = (float)((double)(S[E + 1] - S[t]) * kFxInv);
     for (int j = j0; j < beta; ++j) {
         const bool first32 = !LONG || j < 32;
@@ -349,6 +367,7 @@ __device__ __forceinline__ void forward_walk_f(const FusedParams &p, const Share
         const int ev = __shfl_sync(0xffffffffu, first32 ? rr.e0 : rr.e1, j & 31);
         if ((ev >> 1) != E) {
             E = ev >> 1;
+            if (!DODE_IN_BOUNDS(E + 1, kGroupRoutes + 1, s.err, kSiteGroupSums)) E = t;
             f = (float)((double)(S[E + 1] - S[t]) * kFxInv);
         }
         const int hi = __shfl_down_sync(0xffffffffu, T, 1);
@@ -368,7 +387,7 @@ __device__ __forceinline__ void forward_walk_f(const FusedParams &p, const Share
             }
         }
         T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
-        if (ev & 1) stk[j + 1] = T;
+        if ((ev & 1) && DODE_IN_BOUNDS(j + 1, kMaxRouteLinks + 1, s.err, kSiteWalkStack)) stk[j + 1] = T;
     }
 }
 
@@ -432,6 +451,7 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
     const bool vw = (lane < kTileW) && (b < p.N);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    if (!DODE_IN_BOUNDS(m, kGroupRoutes + 1, s.err, kSiteGroupSums)) return;
     // route flows f = p q (Eq. (flow)) in 2^-20 vehicle units and their
     // exclusive prefix sums over the group's walk order
     long long S[kGroupRoutes + 1];
@@ -444,6 +464,9 @@ __device__ void forward_task(const FusedParams &p, const Shared &s, int day, int
     for (int t = 0; t < m; ++t) {
         const int4 gr = s.groute[i0 + t];
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        if (!DODE_IN_BOUNDS(beta - 1, kMaxRouteLinks, s.err, kSiteWalkStack) ||
+            !DODE_IN_BOUNDS(s0, kMaxRouteLinks + 1, s.err, kSiteWalkStack))
+            continue;
         if (s0 >= beta) continue;                         // every link walked by earlier routes
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bb : nullptr;
@@ -474,6 +497,7 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
                                                 const uint2 *S2, int t, int E, int2 *stk2) {
     const int lane = threadIdx.x & 31;
     const int ipt = p.div.ipt, N = p.Nh;      // horizon: the day, and the first rows of a coupled next day
+    if (!DODE_IN_BOUNDS(E + 1, kGroupRoutes + 1, s.err, kSiteGroupSums)) E = t;
     uint2 shi = S2[E + 1];
     const uint2 slo = S2[t];
     uint32_t WuA = shi.x - slo.x, WuB = shi.y - slo.y;
@@ -484,6 +508,7 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
         const int ev = __shfl_sync(0xffffffffu, rr.e0, j & 31);
         if ((ev >> 1) != E) {
             E = ev >> 1;
+            if (!DODE_IN_BOUNDS(E + 1, kGroupRoutes + 1, s.err, kSiteGroupSums)) E = t;
             shi = S2[E + 1];
             WuA = shi.x - slo.x;
             WuB = shi.y - slo.y;
@@ -540,7 +565,7 @@ __device__ __forceinline__ void forward_walk_u2(const FusedParams &p, const Shar
         }
         TA = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowA, j, TA, tb, h0A);
         TB = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowB, j, TB, tb, h0B);
-        if (ev & 1) stk2[j + 1] = make_int2(TA, TB);
+        if ((ev & 1) && DODE_IN_BOUNDS(j + 1, kMaxRouteLinks + 1, s.err, kSiteWalkStack)) stk2[j + 1] = make_int2(TA, TB);
     }
 }
 
@@ -606,6 +631,7 @@ __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, in
     const bool vwA = (lane < kTileW) && (bA < p.N), vwB = (lane < kTileW) && (bB < p.N);
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    if (!DODE_IN_BOUNDS(m, kGroupRoutes + 1, s.err, kSiteGroupSums)) return;
     uint2 S2[kGroupRoutes + 1];   // the pair walk is integer-form only
     bool any, fast;
     group_flows2<PREC>(p, s, day, i0, m, bA, bB, vwA, vwB, S2, any, fast);
@@ -622,6 +648,9 @@ __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, in
     for (int t = 0; t < m; ++t) {
         const int4 gr = s.groute[i0 + t];
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        if (!DODE_IN_BOUNDS(beta - 1, kMaxRouteLinks, s.err, kSiteWalkStack) ||
+            !DODE_IN_BOUNDS(s0, kMaxRouteLinks + 1, s.err, kSiteWalkStack))
+            continue;
         if (s0 >= beta) continue;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trowA = TAB ? tab + (size_t)(l0 + k) * (p.N + 1) + bbA : nullptr;
@@ -652,6 +681,7 @@ __device__ void forward_task2(const FusedParams &p, const Shared &s, int day, in
 template <int PREC, class RouteK, class RouteGp>
 __device__ __forceinline__ void od_update(const FusedParams &p, int day, int od, int b, int nr, RouteK route_k,
                                           RouteGp route_gp, double &dth) {
+    if (!DODE_IN_BOUNDS(od, p.K, p.err, kSiteDemand) || !DODE_IN_BOUNDS(b, p.N, p.err, kSiteDemand)) return;
     const float *pt = p.pt + (size_t)day * p.P * p.Np;
     float g = 0.f;
     for (int i = 0; i < nr; ++i) g += __ldg(&pt[(size_t)route_k(i) * p.Np + b]) * route_gp(i);
@@ -687,6 +717,7 @@ __device__ __forceinline__ void od_update(const FusedParams &p, int day, int od,
 template <int PREC, class RouteK, class RouteGp2>
 __device__ __forceinline__ void od_step2(const FusedParams &p, int day, int od, int bA, int bB, bool vwA, bool vwB,
                                          int nr, RouteK route_k, RouteGp2 route_gp2) {
+    if (!DODE_IN_BOUNDS(od, p.K, p.err, kSiteDemand)) return;
     const float *pt = p.pt + (size_t)day * p.P * p.Np;
     const size_t row = ((size_t)day * p.K + od) * p.Np;
     const size_t qA = row + (vwA ? bA : 0), qB = row + (vwB ? bB : 0);
@@ -743,10 +774,10 @@ __device__ __forceinline__ float adjoint_walk(const FusedParams &p, const Shared
                 const int e0 = h0 * ipt + ipt;
                 const float inv = __fdividef(1.f, (float)(hi - T));
                 const float d0 = first_share<PREC>(T, e0, inv);
-                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                float a = d0 * rcell<PREC, SMEM_RING>(s, racc, rb, idx);
                 if (hi > e0 && (SMEM_RING || h0 + 1 < N)) {
                     if (hi <= e0 + ipt)
-                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                        a += (1.f - d0) * rcell<PREC, SMEM_RING>(s, racc, rb, idx + 1);
                     else
                         a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hi, e0, h0 + 1, N, ipt, inv,
                                                                  d0, 0.f);
@@ -755,7 +786,7 @@ __device__ __forceinline__ float adjoint_walk(const FusedParams &p, const Shared
             }
         }
         T = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trow, j, T, tb, h0);
-        if (ev & 1) {
+        if ((ev & 1) && DODE_IN_BOUNDS(j + 1, kMaxRouteLinks + 1, s.err, kSiteWalkStack)) {
             stk[j + 1] = T;
             gstk[j + 1] = G;
         }
@@ -778,6 +809,7 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int N = p.N;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    if (!DODE_IN_BOUNDS(m, kGroupRoutes + 1, s.err, kSiteGroupSums)) return;
     float *gp = p.gp + (size_t)blockIdx.x * p.P * p.Np;
     int stk[kMaxRouteLinks + 1];
     float gstk[kMaxRouteLinks + 1];
@@ -785,6 +817,9 @@ __device__ void adjoint_task(const FusedParams &p, const Shared &s, int day, int
     for (int t = 0; t < m; ++t) {
         const int4 gr = s.groute[i0 + t];
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        if (!DODE_IN_BOUNDS(beta - 1, kMaxRouteLinks, s.err, kSiteWalkStack) ||
+            !DODE_IN_BOUNDS(s0, kMaxRouteLinks + 1, s.err, kSiteWalkStack))
+            continue;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trow = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bb : nullptr;
         const int T = walk_start<TAB>(p, trow, stk, s0, bb);
@@ -835,10 +870,10 @@ __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared
                 const int e0 = h0A * ipt + ipt;
                 const float inv = __fdividef(1.f, (float)(hiA - TA));
                 const float d0 = first_share<PREC>(TA, e0, inv);
-                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                float a = d0 * rcell<PREC, SMEM_RING>(s, racc, rb, idx);
                 if (hiA > e0 && (SMEM_RING || h0A + 1 < N)) {
                     if (hiA <= e0 + ipt)
-                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                        a += (1.f - d0) * rcell<PREC, SMEM_RING>(s, racc, rb, idx + 1);
                     else
                         a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiA, e0, h0A + 1, N, ipt, inv,
                                                                  d0, 0.f);
@@ -850,10 +885,10 @@ __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared
                 const int e0 = h0B * ipt + ipt;
                 const float inv = __fdividef(1.f, (float)(hiB - TB));
                 const float d0 = first_share<PREC>(TB, e0, inv);
-                float a = d0 * (SMEM_RING ? racc[idx] : Operand<PREC>::r(rb, (size_t)idx));
+                float a = d0 * rcell<PREC, SMEM_RING>(s, racc, rb, idx);
                 if (hiB > e0 && (SMEM_RING || h0B + 1 < N)) {
                     if (hiB <= e0 + ipt)
-                        a += (1.f - d0) * (SMEM_RING ? racc[idx + 1] : Operand<PREC>::r(rb, (size_t)idx + 1));
+                        a += (1.f - d0) * rcell<PREC, SMEM_RING>(s, racc, rb, idx + 1);
                     else
                         a += window_tail<PREC, SMEM_RING, false>(s, nullptr, rb, idx + 1, hiB, e0, h0B + 1, N, ipt, inv,
                                                                  d0, 0.f);
@@ -863,7 +898,7 @@ __device__ __forceinline__ void adjoint_walk2(const FusedParams &p, const Shared
         }
         TA = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowA, j, TA, tb, h0A);
         TB = next_entry<SMEM_TICKS, TAB>(p, s, tick_day, trowB, j, TB, tb, h0B);
-        if (ev & 1) {
+        if ((ev & 1) && DODE_IN_BOUNDS(j + 1, kMaxRouteLinks + 1, s.err, kSiteWalkStack)) {
             stk2[j + 1] = make_int2(TA, TB);
             gstk2[j + 1] = make_float2(GA, GB);
         }
@@ -883,6 +918,7 @@ __device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, in
     const int32_t *tick_day = p.ticks + (size_t)day * p.A * p.Np;
     const int N = p.N;
     const int i0 = s.gptr[g], m = s.gptr[g + 1] - i0;
+    if (!DODE_IN_BOUNDS(m, kGroupRoutes + 1, s.err, kSiteGroupSums)) return;
     bool longr = false;                                   // a route past 32 links: single-tile walks
     for (int t = 0; t < m; ++t) longr = longr || s.groute[i0 + t].z > 32;
     if (longr) {
@@ -897,6 +933,9 @@ __device__ void adjoint_task2(const FusedParams &p, const Shared &s, int day, in
     for (int t = 0; t < m; ++t) {
         const int4 gr = s.groute[i0 + t];
         const int k = gr.x, l0 = gr.y, beta = gr.z, s0 = gr.w & 0xff;
+        if (!DODE_IN_BOUNDS(beta - 1, kMaxRouteLinks, s.err, kSiteWalkStack) ||
+            !DODE_IN_BOUNDS(s0, kMaxRouteLinks + 1, s.err, kSiteWalkStack))
+            continue;
         const RouteRegs rr = load_route<SMEM_RING, SMEM_TICKS>(p, s, l0, beta);
         const int32_t *trowA = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bbA : nullptr;
         const int32_t *trowB = TAB ? tab + (size_t)(l0 + k) * (N + 1) + bbB : nullptr;
@@ -1035,6 +1074,7 @@ __device__ __forceinline__ void stage_ticks(const FusedParams &p, Shared &s, con
             const int i = i0 + u * blockDim.x;
             if (i < total) {
                 const int a = div_by(i, nch, dn), c = c0 + 8 * (i - a * nch);
+                if (!DODE_IN_BOUNDS(a, p.A, s.err, kSiteStageTicks)) continue;
                 const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
                 uint16_t *row = s.tw + a * s.RW;
 #pragma unroll
@@ -1090,6 +1130,7 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
             v[u] = make_uint4(0u, 0u, 0u, 0u);
             if (i < total) {
                 const int o = div_by(i, nch, dn), c = c0 + E * (i - o * nch);
+                if (!DODE_IN_BOUNDS(o, p.O, s.err, kSiteStageResid)) continue;
                 v[u] = __ldcg(reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(rb) +
                                                             ((size_t)o * p.Np + c) * (PREC == 1 ? 2 : 4)));
             }
@@ -1099,6 +1140,7 @@ __device__ __forceinline__ void stage_residual(const FusedParams &p, Shared &s, 
             const int i = i0 + u * blockDim.x;
             if (i < total) {
                 const int o = div_by(i, nch, dn), c = c0 + E * (i - o * nch);
+                if (!DODE_IN_BOUNDS(o, p.O, s.err, kSiteStageResid)) continue;
                 const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
                 uint32_t *row = s.lo + o * s.R;
 #pragma unroll
@@ -1158,9 +1200,11 @@ __device__ __forceinline__ void flush_phase(const FusedParams &p, const Shared &
                 if (o < p.O && r < rows) {
                     if (SMEM_RING) {
                         const int idx = o * s.R + r;
-                        lo[u] = s.lo[idx];
-                        if (carry) hi[u] = s.hi[idx];
-                    } else {
+                        if (DODE_IN_BOUNDS(idx, s.ring_cells, s.err, kSiteFlushCell)) {
+                            lo[u] = s.lo[idx];
+                            if (carry) hi[u] = s.hi[idx];
+                        }
+                    } else if (DODE_IN_BOUNDS((size_t)o * p.Np + h, s.ring_cells, s.err, kSiteFlushCell)) {
                         float *cell = gacc + (size_t)o * p.Np + h;
                         xf[u] = *cell;
                         *cell = 0.f;
@@ -1254,9 +1298,11 @@ __device__ __forceinline__ void flush_solve(const FusedParams &p, const Shared &
                 if (in) {
                     if (SMEM_RING) {
                         const int idx = o * s.R + r;
-                        const int hw = carry ? s.hi[idx] : 0;
-                        x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
-                    } else {
+                        if (DODE_IN_BOUNDS(idx, s.ring_cells, s.err, kSiteFlushCell)) {
+                            const int hw = carry ? s.hi[idx] : 0;
+                            x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
+                        }
+                    } else if (DODE_IN_BOUNDS(cell + k, s.ring_cells, s.err, kSiteFlushCell)) {
                         x = gacc[cell + k];
                         gacc[cell + k] = 0.f;
                     }
@@ -1343,7 +1389,7 @@ __device__ __forceinline__ void flush_move_solve(const FusedParams &p, const Sha
                 for (int q = 0; q < 4; ++q) {
                     const int r = c + q - pb0;
                     float x = 0.f;
-                    if (r >= 0 && r < span) {
+                    if (r >= 0 && r < span && DODE_IN_BOUNDS(o * s.R + r, s.ring_cells, s.err, kSiteFlushCell)) {
                         const int idx = o * s.R + r;
                         const int hw = carry ? s.hi[idx] : 0;
                         x = fmaf((float)hw, 4096.f, __uint2float_rn(s.lo[idx]) * 9.5367431640625e-7f);
@@ -1388,6 +1434,7 @@ __device__ __forceinline__ void flush_move_solve(const FusedParams &p, const Sha
             uint32_t *lrow = s.lo + o * s.R;
             int *hrow = s.hi + o * s.R;
             for (int r = kq; r < spill; r += L) {
+                if (!DODE_IN_BOUNDS(o * s.R + span + r, s.ring_cells, s.err, kSiteFlushCell)) break;
                 lrow[r] = lrow[span + r];
                 lrow[span + r] = 0u;
                 if (carry) {
@@ -1593,6 +1640,9 @@ __global__ void __launch_bounds__(1024, 1) k_fused(const FusedParams p) {
     __shared__ int s_nrows;
     __shared__ int s_carry;
     s.carry = &s_carry;
+    s.err = p.err;
+    s.ring_cells = SMEM_RING ? p.O * s.R : p.O * p.Np;
+    s.tick_cells = SMEM_TICKS ? p.A * s.RW : p.A * p.Np;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nthr = blockDim.x;

@@ -19,13 +19,14 @@ LIB_PATH = os.path.join(HERE, "libdode.so")
 OK = 0
 ERR_ARG, ERR_ROUTE_NOT_CONTIGUOUS, ERR_ROUTE_REPEATS_LINK, ERR_BAD_SPEED = -1, -2, -3, -4
 ERR_TICK_OVERFLOW, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = -5, -6, -7, -8, -9, -10
+ERR_BOUNDS = -11
 PTR_HOST, PTR_DEVICE = 0, 1
 FORM_FUSED, FORM_PLAIN = 0, 1
 PREC_FP32, PREC_BF16 = 0, 1
 
 _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_ROUTE_REPEATS_LINK",
               -4: "ERR_BAD_SPEED", -5: "ERR_TICK_OVERFLOW", -6: "ERR_OOM", -7: "ERR_CUDA",
-              -8: "ERR_DEVICE_TIMEOUT", -9: "ERR_STATE", -10: "ERR_UNSUPPORTED"}
+              -8: "ERR_DEVICE_TIMEOUT", -9: "ERR_STATE", -10: "ERR_UNSUPPORTED", -11: "ERR_BOUNDS"}
 
 # every entry point of include/dode.h
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
@@ -69,11 +70,14 @@ class dode_options(ct.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libdode.so (built in-tree by ``build.py``); raises if it is absent."""
+def load(path: Optional[str] = None):
+    """Load libdode.so (built in-tree by ``build.py``); raises if it is absent.
+    The environment variable DODE_LIB selects another build of the same library
+    (the index-checked debug build of ``build.build(checked=True)``)."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("DODE_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"libdode.so not built at {path}; run paper_1901_09266_gb300.build.build()")
     L = ct.CDLL(path)
