@@ -257,12 +257,21 @@ int dode_last_totals(dode_ctx *ctx, double *loss_total, double *dtheta_total);
  *              with a grid-wide step between passes; needs m = 1,
  *              n_cols % 4 == 0, n_cols <= 8192, a 16-byte aligned B and a device
  *              that supports cooperative launches, else DODE_ERR_UNSUPPORTED),
- *              2 = two passes (one per product).  Automatic takes one pass when
- *              it applies.
+ *              2 = two passes (one per product), 3 = tensor cores: the m
+ *              right-hand sides stacked into two GEMMs per iteration (R = B X - Y,
+ *              then B^T R) with TF32 operands and FP32 accumulation, split-K
+ *              partials summed in a fixed order, the iterations replayed as a
+ *              CUDA graph; needs m a multiple of 16 in 16..256, n_rows and
+ *              n_cols multiples of 4 and, for device pointers, 16-byte aligned
+ *              B and Y, else DODE_ERR_UNSUPPORTED.  TF32 keeps 10 mantissa bits
+ *              of each operand, so the iterates differ from those of the FP32
+ *              methods by up to about 1e-2 relative.  Automatic takes one pass
+ *              when it applies, else two.
  *   kernel_ms  out (may be NULL): GPU time of the iterations and the final residual
  * All arrays are host or device pointers per ptr_kind; stream is a cudaStream_t
  * (NULL = default stream); the call returns when its work is complete.
- * Limits: 1 <= m <= 8 and n_cols * m <= 51200 (x is staged in shared memory).
+ * Limits: methods 0-2: 1 <= m <= 8 and n_cols * m <= 51200 (x is staged in
+ * shared memory); method 3: 16 <= m <= 256.
  * Errors: DODE_ERR_ARG, DODE_ERR_UNSUPPORTED (the limits), DODE_ERR_OOM, DODE_ERR_CUDA,
  * DODE_ERR_DEVICE_TIMEOUT (a bounded device wait of the one-pass kernel ran out: a
  * row copy, or the grid-wide step); the message goes to stderr.  After a timeout
