@@ -706,10 +706,33 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fused launch from an ncu capture of the same kernel")
+    ap.add_argument("--dense-case", default="",
+                    help="METHOD,M: run one dense NNLS call (n = --dense-n, --dense-iters iterations) and exit; "
+                         "the small case the dense kernels' profiles capture")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.dense_case:
+        return run_dense_case(args)
     return run_gpu(args)
+
+
+def run_dense_case(args):
+    """One dode_dense_nnls call on the benchmark's dense input (seeded random n x n B, y = B x with
+    x >= 0, m columns), printed as one JSON line: the case an ncu capture of a dense kernel runs."""
+    import torch
+    from paper_1901_09266_gb300 import build, dode
+    build.build()
+    method, m = (int(v) for v in args.dense_case.split(","))
+    n = args.dense_n
+    rng = np.random.default_rng(1901)
+    B = torch.from_numpy(rng.standard_normal((n, n), dtype=np.float32) / np.float32(np.sqrt(n))).cuda()
+    X0 = torch.from_numpy(np.abs(rng.standard_normal((n, m))).astype(np.float32)).cuda()
+    Y = (B @ X0).contiguous()
+    _, _, loss, ms = dode.dense_nnls(B, Y, args.dense_iters, 0.05, method=method)
+    print(json.dumps({"dense_case": {"method": method, "n": n, "m": m, "iters": args.dense_iters,
+                                     "kernel_ms": ms, "loss": float(loss.double().sum().item())}}))
+    return 0
 
 
 if __name__ == "__main__":

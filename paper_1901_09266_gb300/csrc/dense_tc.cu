@@ -42,12 +42,12 @@ namespace dode {
 
 constexpr int kTcM = 128;                 // rows per tile (TMEM lanes)
 constexpr int kTcK = 32;                  // K per tile: 32 FP32 = one 128-byte swizzle row
-constexpr int kTcStages = 4;              // ring stages at most (fewer when they do not fit in shared memory)
+constexpr int kTcStages = 8;              // ring stages at most (fewer when they do not fit in shared memory)
 constexpr int kTcThreads = 256;
 constexpr int kTcRedCols = 8;             // columns per block of the reduce-and-epilogue kernel
 constexpr long long kTcWait = 1ll << 26;
 
-enum TcEpi : int { TC_RESID = 0, TC_STEP = 1 };
+enum TcEpi : int { TC_RESID = 0, TC_STEP = 1, TC_RESID_ONLY = 2 };
 
 struct TcParams {
     int M, K, N;                          // C [M][N] = A [M][K] Bop[N][K]^T
@@ -286,6 +286,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // (M tile, kTcRedCols columns), thread = row of the tile; narrow column blocks
 // give enough blocks to hide the partials' load latency.
 //   TC_RESID: Rt[j][i] = C[i][j] - Y[i][j]; lpart[tile][j] = sum over the tile's rows of r^2
+//   TC_RESID_ONLY: Rt alone (the iterations before the last need no loss, and
+//            its FP64 warp sums run on the slow FP64 pipe)
 //   TC_STEP:  Gt[j][i] += g^2, Xt[j][i] = max(Xt[j][i] - eta g / (sqrt(Gt) + eps), 0) with g = C[i][j]
 template <int EPI>
 __global__ void __launch_bounds__(kTcM) k_tc_reduce(const TcParams p) {
@@ -319,6 +321,8 @@ __global__ void __launch_bounds__(kTcM) k_tc_reduce(const TcParams p) {
                 }
                 for (int off = 16; off > 0; off >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, off);
                 if (lane == 0) red[w][jq + q] = l2;
+            } else if (EPI == TC_RESID_ONLY) {
+                if (live) p.Rt[(size_t)j * p.M + row] = c[q] - __ldg(p.Yt + (size_t)j * p.M + row);
             } else if (live) {
                 const size_t e = (size_t)j * p.M + row;
                 const float g = c[q];
@@ -494,7 +498,7 @@ int dense_tc_nnls(int nr, int nc, int m, const float *B, const float *Y, int ite
     if (e == cudaSuccess) {
         cudaError_t ec = cudaSuccess;
         for (int it = 0; it < iters && ec == cudaSuccess; ++it) {
-            ec = tc_launch<TC_RESID>(tB, tXt, p1, g1, cs);
+            ec = tc_launch<TC_RESID_ONLY>(tB, tXt, p1, g1, cs);
             if (ec == cudaSuccess) ec = tc_launch<TC_STEP>(tBt, tRt, p2, g2, cs);
         }
         if (ec == cudaSuccess) ec = tc_launch<TC_RESID>(tB, tXt, p1, g1, cs);    // residual and loss of the final X
