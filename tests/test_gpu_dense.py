@@ -98,7 +98,7 @@ def test_dense_one_pass_wait_runs_out_then_recovers():
         dode.dense_set_wait_limit(-1)
 
 
-@pytest.mark.parametrize("nr,nc,m", [(512, 512, 16), (1000, 764, 64), (260, 1024, 256), (4, 36, 32)])
+@pytest.mark.parametrize("nr,nc,m", [(512, 512, 16), (1000, 764, 64), (260, 1024, 256), (300, 640, 128), (4, 36, 32)])
 def test_dense_tensor_cores_match_tf32_oracle(nr, nc, m):
     """Many right-hand sides stacked into GEMMs on the tensor cores (method 3:
     tcgen05 with TF32 operands and FP32 accumulation).  Against the oracle's
