@@ -452,11 +452,10 @@ def run_gpu(args):
                                      else None),
             "final_loss_rel_diff": abs(f16["final_loss"] - f32["final_loss"]) / f32["final_loss"]}
 
-    # BASELINE config 3: uneven days (per-day observed subsets, missing rates
-    # U(0, 30 %)) in one persistent launch, the launch shape picked by the
-    # autotuner, direct launches against CUDA-graph replay, for days per launch
-    # swept over 1 .. 1096
-    config3 = None
+    # uneven days (per-day observed subsets, missing rates U(0, 30 %)) in one
+    # persistent launch, the launch shape picked by the autotuner, direct
+    # launches against CUDA-graph replay, for days per launch swept over 1 .. 1096
+    uneven_sweep = None
     if args.uneven_sweep and rank == 0:
         from paper_1901_09266_gb300 import autotune
         wu = make_workload("corridor-uneven", max(args.uneven_days))
@@ -491,7 +490,7 @@ def run_gpu(args):
                     "final_loss": float(ln.double().sum().item())}
                 cu.close()
             points.append(pt_)
-        config3 = {"workload": wu.name, "epochs": args.uneven_epochs, "precision": args.precision,
+        uneven_sweep = {"workload": wu.name, "epochs": args.uneven_epochs, "precision": args.precision,
                    "observed_links_per_day": [int(x) for x in (mku.reshape(len(du), N, O).any(axis=1).sum(axis=1)
                                                                [[0, -1]])],
                    "points": points}
@@ -583,13 +582,13 @@ def run_gpu(args):
         nxt["dense_nnls"]["tensor_cores"] = tc
         del Bd, Yd
 
-    # form 3 (differentiable) on the 600-OD / 1500-route / 1000-detector corridor:
+    # the differentiable loss and gradients on the 600-OD / 1500-route / 1000-detector corridor:
     # loss and gradients (dL/dq, dL/dtheta) of every day, DAR recomputed in both
     # passes, in FP32 and BF16
-    form3 = None
-    if args.form3_days > 0 and rank == 0:
-        w5 = make_workload("corridor-large", args.form3_days)
-        d5 = list(range(args.form3_days))
+    loss_grad_large = None
+    if args.loss_grad_days > 0 and rank == 0:
+        w5 = make_workload("corridor-large", args.loss_grad_days)
+        d5 = list(range(args.loss_grad_days))
         sp5, ct5, mk5 = gpu_inputs(w5, d5)
         sp5_d, ct5_d, mk5_d = (torch.from_numpy(a).to(dev) for a in (sp5, ct5, mk5))
         q5 = torch.from_numpy(w5.q_true(d5) * np.float32(0.9)).to(dev)
@@ -598,7 +597,7 @@ def run_gpu(args):
         # bytes one loss+gradient pass of a day must move: counts, mask bits,
         # uint16 ticks, q read, dL/dq written, loss and dL/dtheta
         per5 = 4 * N5 * O5 + (N5 * O5) // 8 + 2 * N5 * A5 + 4 * N5 * K5 + 4 * N5 * K5 + 16
-        form3 = {"workload": w5.name, "days": len(d5), "routes": w5.routes.n_routes, "od_pairs": K5,
+        loss_grad_large = {"workload": w5.name, "days": len(d5), "routes": w5.routes.n_routes, "od_pairs": K5,
                  "detectors": O5, "bytes_per_day_pass": per5}
         res5 = {}
         for pname, pr in (("fp32", dode.PREC_FP32), ("bf16", dode.PREC_BF16)):
@@ -614,13 +613,13 @@ def run_gpu(args):
             res5[pname] = (np.asarray(loss5, np.float64), dq5.detach().cpu().numpy().astype(np.float64),
                            np.asarray(dth5, np.float64))
             pk_gbs = peak if peak else 6800.0
-            form3[pname] = {"kernel_ms": t5 * 1e3, "day_loss_grads_per_s": len(d5) / t5,
+            loss_grad_large[pname] = {"kernel_ms": t5 * 1e3, "day_loss_grads_per_s": len(d5) / t5,
                             "roofline": {"bound": "hbm", "achieved": per5 * len(d5) / t5 / 1e9, "peak": pk_gbs,
                                          "unit": "GB/s", "frac": per5 * len(d5) / t5 / 1e9 / pk_gbs},
                             "total_loss": float(np.sum(loss5)), "dtheta_total": float(np.sum(dth5))}
             c5.close()
         (l32, g32, t32), (l16, g16, t16) = res5["fp32"], res5["bf16"]
-        form3["bf16_vs_fp32"] = {
+        loss_grad_large["bf16_vs_fp32"] = {
             "loss_max_rel": float(np.max(np.abs(l16 - l32) / np.abs(l32))),
             "dq_max_rel_norm": float(np.max(np.sqrt(((g16 - g32) ** 2).sum(axis=(1, 2)) / (g32 ** 2).sum(axis=(1, 2))))),
             "dtheta_max_rel": float(np.max(np.abs(t16 - t32) / np.abs(t32)))}
@@ -655,8 +654,8 @@ def run_gpu(args):
             "clocks": clk,
             "forms": forms,
             "next": nxt,
-            "config3": config3,
-            "form3": form3,
+            "uneven_sweep": uneven_sweep,
+            "loss_grad_large": loss_grad_large,
             "final_loss_total": final_loss,
         }
         print(json.dumps(line), flush=True)
@@ -689,7 +688,7 @@ def main(argv=None):
     ap.add_argument("--autotune", action="store_true", help="pick the launch shape with the autotuner")
     ap.add_argument("--compare-epochs", type=int, default=20)
     ap.add_argument("--next-rows", type=int, default=1, help="time the pattern, R^2, DAR-distance and dense rows")
-    ap.add_argument("--form3-days", type=int, default=1096,
+    ap.add_argument("--loss-grad-days", type=int, default=1096,
                     help="days of the corridor-large loss+gradient timing (0 = skip)")
     ap.add_argument("--uneven-sweep", type=int, default=1,
                     help="time the uneven-day workload over --uneven-days days per launch (0 = skip)")
