@@ -21,7 +21,9 @@
 //
 // Per CTA (persistent over work items):
 //   warp 0   TMEM allocation; one lane issues the TMA tile loads (A: 128 x 32,
-//            Bop: m x 32, 128-byte swizzle) into a ring of S stages (full[s])
+//            Bop: m x 32, 128-byte swizzle) into a ring of S stages (full[s]),
+//            each holding kt consecutive K tiles (kt = 2 for m <= 64: every row
+//            of A is then read in 256-byte runs)
 //   warp 1   one lane issues the MMAs (four K = 8 steps per 32-wide K tile) into
 //            one of two TMEM accumulators and commits them to the stage's
 //            empty[s] barrier, and after the tile's last K step to tfull[a]
@@ -54,6 +56,9 @@ struct TcParams {
     int m_tiles, k_tiles;
     int ksplit, kpc;                      // split-K: work item = (M tile, K range of kpc tiles)
     int stages;                           // ring stages in use (<= kTcStages)
+    int kt;                               // K tiles per stage (1 or 2, the kernel's template argument): with
+                                          // 2, each row of A is read in 256-byte runs, which DRAM serves
+                                          // with fewer row activations
     float *part;                          // [m_tiles * ksplit][N][128] partial products
     uint32_t idesc;                       // tcgen05 instruction descriptor
     // TC_RESID: Rt[j][i] = C[i][j] - Y[i][j], lpart[tile][j] = sum over the
@@ -95,6 +100,7 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+template <int KT>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -106,7 +112,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // 1024-byte aligned stages: A tile then Bop tile
     const uint32_t sbase = (tc_smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t a_bytes = kTcM * kTcK * 4, b_bytes = (uint32_t)p.N * kTcK * 4;
-    const uint32_t stage_bytes = (a_bytes + b_bytes + 1023u) & ~1023u;
+    // a stage holds KT consecutive K tiles: A tiles first, then Bop tiles
+    constexpr int kt = KT;
+    const uint32_t stage_bytes = ((uint32_t)kt * (a_bytes + b_bytes) + 1023u) & ~1023u;
     const int ncols = p.N * 2 <= 32 ? 32 : (p.N * 2 <= 64 ? 64 : (p.N * 2 <= 128 ? 128 : (p.N * 2 <= 256 ? 256 : 512)));
 
     if (tid == 0) {
@@ -150,28 +158,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int item = blockIdx.x + lt * gridDim.x, tile = item / p.ksplit;
             int kb, nk, rot;
             krange(item, kb, nk, rot);
-            for (int jk = 0; jk < nk; ++jk, ++it) {
-                const int k = kb + (jk + rot) % nk;
+            for (int jk = 0; jk < nk; jk += kt, ++it) {
+                const int nt = KT == 1 ? 1 : min(kt, nk - jk);
                 const int s = (int)(it % S);
                 if (it >= S && !tc_wait(&empty[s], (uint32_t)((it / S - 1) & 1), &abort_cta)) {
                     abort_cta = 1;
                     atomicCAS(p.err, 0, kErrDeviceTimeout);
                     break;
                 }
-                const uint32_t sa = sbase + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
+                const uint32_t sa = sbase + (uint32_t)s * stage_bytes, sb = sa + (uint32_t)kt * a_bytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(&full[s])),
-                             "r"(a_bytes + b_bytes)
+                             "r"((uint32_t)nt * (a_bytes + b_bytes))
                              : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                    "[%4];" ::"r"(sa),
-                    "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(k * kTcK), "r"(tile * kTcM), "r"(tc_smem_u32(&full[s]))
-                    : "memory");
-                asm volatile(
-                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                    "[%4];" ::"r"(sb),
-                    "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(k * kTcK), "r"(0), "r"(tc_smem_u32(&full[s]))
-                    : "memory");
+                if constexpr (KT == 1) {
+                    const int k = kb + (jk + rot) % nk;
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                        "%3}], [%4];" ::"r"(sa),
+                        "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(k * kTcK), "r"(tile * kTcM),
+                        "r"(tc_smem_u32(&full[s]))
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                        "%3}], [%4];" ::"r"(sb),
+                        "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(k * kTcK), "r"(0), "r"(tc_smem_u32(&full[s]))
+                        : "memory");
+                } else {
+                    for (int t = 0; t < nt; ++t) {
+                        const int k = kb + (jk + t + rot) % nk;
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                            "%3}], [%4];" ::"r"(sa + (uint32_t)t * a_bytes),
+                            "l"(reinterpret_cast<uint64_t>(&tmA)), "r"(k * kTcK), "r"(tile * kTcM),
+                            "r"(tc_smem_u32(&full[s]))
+                            : "memory");
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                            "%3}], [%4];" ::"r"(sb + (uint32_t)t * b_bytes),
+                            "l"(reinterpret_cast<uint64_t>(&tmB)), "r"(k * kTcK), "r"(0), "r"(tc_smem_u32(&full[s]))
+                            : "memory");
+                    }
+                }
                 issued = it + 1;
             }
         }
@@ -196,7 +223,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             int kb, nk, rot;
             krange(blockIdx.x + lt * gridDim.x, kb, nk, rot);
-            for (int k = 0; k < nk; ++k, ++it) {
+            for (int jk = 0; jk < nk; jk += kt, ++it) {
+                const int nt = KT == 1 ? 1 : min(kt, nk - jk);
                 const int s = (int)(it % S);
                 if (!tc_wait(&full[s], (uint32_t)((it / S) & 1), &abort_cta)) {
                     abort_cta = 1;
@@ -205,17 +233,34 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = sbase + (uint32_t)s * stage_bytes, sb = sa + a_bytes;
+                const uint32_t sa = sbase + (uint32_t)s * stage_bytes, sb = sa + (uint32_t)kt * a_bytes;
+                if constexpr (KT == 1) {
 #pragma unroll
-                for (int kk = 0; kk < kTcK / 8; ++kk) {
-                    // K = 8 TF32 elements = 32 bytes per MMA: advance the start addresses
-                    const uint64_t ad = tc_desc(sa + 32u * kk), bd = tc_desc(sb + 32u * kk);
-                    const uint32_t acc = (k > 0 || kk > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                        "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc)
-                        : "memory");
+                    for (int kk = 0; kk < kTcK / 8; ++kk) {
+                        // K = 8 TF32 elements = 32 bytes per MMA: advance the start addresses
+                        const uint64_t ad = tc_desc(sa + 32u * kk), bd = tc_desc(sb + 32u * kk);
+                        const uint32_t acc = (jk > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc)
+                            : "memory");
+                    }
+                } else {
+                    for (int t = 0; t < nt; ++t) {
+#pragma unroll
+                        for (int kk = 0; kk < kTcK / 8; ++kk) {
+                            // K = 8 TF32 elements = 32 bytes per MMA: advance the start addresses
+                            const uint64_t ad = tc_desc(sa + (uint32_t)t * a_bytes + 32u * kk),
+                                           bd = tc_desc(sb + (uint32_t)t * b_bytes + 32u * kk);
+                            const uint32_t acc = (jk > 0 || t > 0 || kk > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                                "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc)
+                                : "memory");
+                        }
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  tc_smem_u32(&empty[s]))
@@ -402,17 +447,29 @@ static uint32_t tc_idesc(int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
-static size_t tc_stage_bytes(int N) { return ((size_t)kTcM * kTcK * 4 + (size_t)N * kTcK * 4 + 1023) & ~(size_t)1023; }
+static size_t tc_stage_bytes(int N, int kt) {
+    return ((size_t)kt * ((size_t)kTcM * kTcK * 4 + (size_t)N * kTcK * 4) + 1023) & ~(size_t)1023;
+}
 
 // stages that fit beside the kernel's static shared memory (about 200 KB of ring)
-static int tc_stages(int N) { return (int)std::max<size_t>(2, std::min<size_t>(kTcStages, (200u << 10) / tc_stage_bytes(N))); }
+static int tc_stages(int N, int kt) {
+    return (int)std::max<size_t>(2, std::min<size_t>(kTcStages, (200u << 10) / tc_stage_bytes(N, kt)));
+}
 
-static size_t tc_smem(int N) { return tc_stage_bytes(N) * tc_stages(N) + 1024; }
+// two K tiles per stage while at least four such stages fit (m <= 64: n = 6000 80.8 -> 72.8 us,
+// n = 8000 136.7 -> 107.7 us per iteration at m = 64), else one (at m = 256 two tiles leave only two
+// stages: 93.8 -> 103.5 us)
+static int tc_kt(int N) { return (200u << 10) / tc_stage_bytes(N, 2) >= 4 ? 2 : 1; }
+
+static size_t tc_smem(int N) { return tc_stage_bytes(N, tc_kt(N)) * tc_stages(N, tc_kt(N)) + 1024; }
 
 // One product: the GEMM's partial products, then their fixed-order sum and the epilogue.
 template <int EPI>
 static cudaError_t tc_launch(const CUtensorMap &a, const CUtensorMap &b, const TcParams &p, int grid, cudaStream_t s) {
-    k_tc_gemm<<<grid, kTcThreads, tc_smem(p.N), s>>>(a, b, p);
+    if (p.kt == 2)
+        k_tc_gemm<2><<<grid, kTcThreads, tc_smem(p.N), s>>>(a, b, p);
+    else
+        k_tc_gemm<1><<<grid, kTcThreads, tc_smem(p.N), s>>>(a, b, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_tc_reduce<EPI><<<dim3(p.m_tiles, (p.N + kTcRedCols - 1) / kTcRedCols), kTcM, 0, s>>>(p);
@@ -482,14 +539,16 @@ int dense_tc_nnls(int nr, int nc, int m, const float *B, const float *Y, int ite
         pp->kpc = (pp->k_tiles + pp->ksplit - 1) / pp->ksplit;
         pp->ksplit = (pp->k_tiles + pp->kpc - 1) / pp->kpc;
         pp->part = part;
-        pp->stages = tc_stages(m);
+        pp->kt = tc_kt(m);
+        pp->stages = tc_stages(m, pp->kt);
     }
     const int g1 = std::min(n_sm, mt1 * p1.ksplit), g2 = std::min(n_sm, mt2 * p2.ksplit);
     // the iterations' launches (four per iteration) are captured once into a CUDA
     // graph on a private stream and replayed on the caller's: the host then
     // issues one launch instead of 4 iters + 3
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(m));
+        e = cudaFuncSetAttribute(tc_kt(m) == 2 ? (const void *)k_tc_gemm<2> : (const void *)k_tc_gemm<1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem(m));
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
