@@ -22,7 +22,7 @@
 // Per CTA (persistent over work items):
 //   warp 0   TMEM allocation; one lane issues the TMA tile loads (A: 128 x 32,
 //            Bop: m x 32, 128-byte swizzle) into a ring of S stages (full[s]),
-//            each holding kt consecutive K tiles (kt = 2 for m <= 64: every row
+//            each holding kt consecutive K tiles (kt = 2 for m <= 128: every row
 //            of A is then read in 256-byte runs)
 //   warp 1   one lane issues the MMAs (four K = 8 steps per 32-wide K tile) into
 //            one of two TMEM accumulators and commits them to the stage's
@@ -456,10 +456,10 @@ static int tc_stages(int N, int kt) {
     return (int)std::max<size_t>(2, std::min<size_t>(kTcStages, (200u << 10) / tc_stage_bytes(N, kt)));
 }
 
-// two K tiles per stage while at least four such stages fit (m <= 64: n = 6000 80.8 -> 72.8 us,
-// n = 8000 136.7 -> 107.7 us per iteration at m = 64), else one (at m = 256 two tiles leave only two
-// stages: 93.8 -> 103.5 us)
-static int tc_kt(int N) { return (200u << 10) / tc_stage_bytes(N, 2) >= 4 ? 2 : 1; }
+// two K tiles per stage while at least three such stages fit (m <= 128; per iteration at
+// n = 6000 / 8000: m = 64 80.8 -> 72.8 / 136.7 -> 107.7 us, m = 128 85.0 -> 79.1 / 139.9 -> 116.2 us),
+// else one (at m = 256 two tiles leave only two stages: 93.8 -> 103.5 us)
+static int tc_kt(int N) { return (200u << 10) / tc_stage_bytes(N, 2) >= 3 ? 2 : 1; }
 
 static size_t tc_smem(int N) { return tc_stage_bytes(N, tc_kt(N)) * tc_stages(N, tc_kt(N)) + 1024; }
 
