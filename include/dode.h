@@ -174,6 +174,21 @@ int dode_create(const dode_network *net, const dode_routes *routes, const dode_o
 int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const float *speeds,
                   const uint8_t *mask, int32_t ptr_kind);
 
+/*
+ * dode_prefetch_days -- start copying the next batch of days to the device
+ * while the current one solves.  Host pointers, same layouts as dode_set_days;
+ * pinned host memory makes the copies asynchronous.  The copies run on a
+ * stream of the context's own and the call returns at once.  The next
+ * dode_set_days with DODE_PTR_HOST and the same n_days, counts, speeds and
+ * mask pointers waits for them and uses the device copies instead of copying
+ * again; a dode_set_days with other inputs lets them finish and ignores them.
+ * The host buffers must stay valid and unchanged until that dode_set_days
+ * call.  Keeps one device copy of the inputs (D N (n_links + n_obs) 4 bytes +
+ * D N n_obs for the mask).  Errors: DODE_ERR_ARG, DODE_ERR_OOM, DODE_ERR_CUDA.
+ */
+int dode_prefetch_days(dode_ctx *ctx, int32_t n_days, const float *counts, const float *speeds,
+                       const uint8_t *mask);
+
 /* Replace the counts (and mask, if not NULL) of the loaded days; speeds and
  * solver state are kept.  Same layouts as dode_set_days. */
 int dode_set_counts(dode_ctx *ctx, const float *counts, const uint8_t *mask, int32_t ptr_kind);

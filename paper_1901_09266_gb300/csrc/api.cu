@@ -109,6 +109,15 @@ struct dode_ctx {
     // CUDA graph of dode_solve's device work (use_graph)
     cudaGraphExec_t graph_exec = nullptr;
     int graph_slices = 1;                  // epoch slices of the captured solve
+    // the next batch of days copied ahead (dode_prefetch_days): [speeds | counts | mask]
+    char *d_pref = nullptr;
+    size_t pref_cap = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pref_ev = nullptr;
+    bool pref_pending = false;
+    int pref_D = 0;
+    const void *pref_src[3] = {nullptr, nullptr, nullptr};   // speeds, counts, mask of the pending copy
+    size_t pref_off[3] = {0, 0, 0};
     cudaStream_t own_stream = nullptr;     // capture stream when the context uses the legacy default stream
     struct GraphKey {
         int iters = -1, grid = 0, block = 0, ring = 0, tick = 0, F = 0, prec = -1;
@@ -1113,6 +1122,12 @@ void dode_destroy(dode_ctx *ctx) {
     dfree(ctx->d_rc_key);
     dfree(ctx->d_rc_row);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->pref_ev) {
+        cudaEventSynchronize(ctx->pref_ev);
+        cudaEventDestroy(ctx->pref_ev);
+    }
+    if (ctx->d_pref) cudaFree(ctx->d_pref);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -1135,12 +1150,69 @@ int dode_set_launch(dode_ctx *ctx, int32_t block_threads, int32_t ctas_per_sm) {
     return DODE_OK;
 }
 
+int dode_prefetch_days(dode_ctx *ctx, int32_t n_days, const float *counts, const float *speeds,
+                       const uint8_t *mask) {
+    if (!ctx) return DODE_ERR_ARG;
+    if (n_days < 1 || !counts || !speeds) return fail(ctx, DODE_ERR_ARG, "prefetch_days arguments");
+    int rc = set_device(ctx);
+    if (rc) return rc;
+    if (ctx->pref_pending) {                      // the previous copy must land before its buffer is reused
+        CU(cudaEventSynchronize(ctx->pref_ev));
+        ctx->pref_pending = false;
+    }
+    const size_t D = (size_t)n_days, N = ctx->N;
+    const size_t sp_bytes = D * N * ctx->A * sizeof(float), ct_bytes = D * N * ctx->O * sizeof(float);
+    const size_t mk_bytes = mask ? D * N * ctx->O : 0;
+    auto align256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t off_ct = align256(sp_bytes), off_mk = off_ct + align256(ct_bytes);
+    const size_t need = off_mk + mk_bytes;
+    if (need > ctx->pref_cap) {
+        if (ctx->d_pref) cudaFree(ctx->d_pref);
+        ctx->d_pref = nullptr;
+        ctx->pref_cap = 0;
+        if (cudaMalloc(&ctx->d_pref, need) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(ctx, DODE_ERR_OOM, "prefetch buffer");
+        }
+        ctx->pref_cap = need;
+    }
+    if (!ctx->copy_stream) CU(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    if (!ctx->pref_ev) CU(cudaEventCreateWithFlags(&ctx->pref_ev, cudaEventDisableTiming));
+    CU(cudaMemcpyAsync(ctx->d_pref, speeds, sp_bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    CU(cudaMemcpyAsync(ctx->d_pref + off_ct, counts, ct_bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    if (mask) CU(cudaMemcpyAsync(ctx->d_pref + off_mk, mask, mk_bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+    CU(cudaEventRecord(ctx->pref_ev, ctx->copy_stream));
+    ctx->pref_pending = true;
+    ctx->pref_D = n_days;
+    ctx->pref_src[0] = speeds;
+    ctx->pref_src[1] = counts;
+    ctx->pref_src[2] = mask;
+    ctx->pref_off[0] = 0;
+    ctx->pref_off[1] = off_ct;
+    ctx->pref_off[2] = off_mk;
+    return DODE_OK;
+}
+
 int dode_set_days(dode_ctx *ctx, int32_t n_days, const float *counts, const float *speeds, const uint8_t *mask,
                   int32_t ptr_kind) {
     if (!ctx) return DODE_ERR_ARG;
     if (n_days < 1 || !counts || !speeds || bad_ptr_kind(ptr_kind)) return fail(ctx, DODE_ERR_ARG, "set_days arguments");
     int rc = set_device(ctx);
     if (rc) return rc;
+    if (ctx->pref_pending) {
+        // host buffers copied ahead by dode_prefetch_days: take the device copies
+        if (ptr_kind == DODE_PTR_HOST && n_days == ctx->pref_D && speeds == ctx->pref_src[0] &&
+            counts == ctx->pref_src[1] && mask == ctx->pref_src[2]) {
+            CU(cudaStreamWaitEvent(ctx->stream, ctx->pref_ev, 0));
+            speeds = reinterpret_cast<const float *>(ctx->d_pref + ctx->pref_off[0]);
+            counts = reinterpret_cast<const float *>(ctx->d_pref + ctx->pref_off[1]);
+            if (mask) mask = reinterpret_cast<const uint8_t *>(ctx->d_pref + ctx->pref_off[2]);
+            ptr_kind = DODE_PTR_DEVICE;
+        } else {
+            CU(cudaEventSynchronize(ctx->pref_ev));   // other inputs: the copy is not used
+        }
+        ctx->pref_pending = false;
+    }
     CU(cudaStreamSynchronize(ctx->stream));
     const int D = n_days, N = ctx->N, Np = ctx->Np, A = ctx->A, O = ctx->O;
     if (D != ctx->D) {

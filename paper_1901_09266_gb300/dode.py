@@ -32,7 +32,7 @@ _ERR_NAMES = {0: "OK", -1: "ERR_ARG", -2: "ERR_ROUTE_NOT_CONTIGUOUS", -3: "ERR_R
 EXPORTS = ("dode_default_options", "dode_create", "dode_set_days", "dode_set_counts", "dode_solve",
            "dode_get_loss_trace", "dode_get_state", "dode_set_state", "dode_forward", "dode_loss",
            "dode_loss_grad", "dode_last_totals", "dode_dense_nnls", "dode_dense_set_wait_limit", "dode_set_patterns", "dode_r2", "dode_dar_distance", "dode_loss_static_scratch", "dode_get_ticks", "dode_get_route_times", "dode_get_day_info", "dode_get_dar",
-           "dode_last_kernel_ms", "dode_last_launches", "dode_last_grid", "dode_last_slices", "dode_total_launches", "dode_device", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
+           "dode_last_kernel_ms", "dode_last_launches", "dode_last_grid", "dode_last_slices", "dode_prefetch_days", "dode_total_launches", "dode_device", "dode_set_launch", "dode_set_max_ctas", "dode_set_stream",
            "dode_last_error", "dode_destroy")
 
 
@@ -109,6 +109,7 @@ def load(path: Optional[str] = None):
         "dode_last_kernel_ms": (f64, [vp]),
         "dode_last_launches": (i64, [vp]),
         "dode_last_grid": (i32, [vp]),
+        "dode_prefetch_days": (ct.c_int, [vp, i32, vp, vp, vp]),
         "dode_last_slices": (i32, [vp]),
         "dode_device": (i32, [vp]),
         "dode_total_launches": (i64, [vp]),
@@ -249,6 +250,20 @@ class Context:
         kind = self._same_kind((kc_, True), (ks_, True), (km_, mask is not None))
         self._check(load().dode_set_days(self.h, D, pc, ps, pm, kind))
         self.D = D
+
+    def prefetch_days(self, counts, speeds, mask=None) -> None:
+        """``dode_prefetch_days``: start copying the next batch of days (host arrays,
+        pinned for overlap) to the device; the next ``set_days`` with the same
+        arrays uses the copies.  The arrays are kept alive until then."""
+        ct, sp = _host(counts, np.float32), _host(speeds, np.float32)
+        mk = None if mask is None else _host(mask, np.uint8)
+        D = ct.shape[0]
+        if ct.shape != (D, self.N, self.O) or sp.shape != (D, self.N, self.A) or (
+                mk is not None and mk.shape != (D, self.N, self.O)):
+            raise ValueError("prefetch_days: counts [D][N][n_obs], speeds [D][N][n_links], mask [D][N][n_obs]")
+        self._pref_keep = (ct, sp, mk)
+        self._check(load().dode_prefetch_days(self.h, D, ct.ctypes.data, sp.ctypes.data,
+                                              None if mk is None else mk.ctypes.data))
 
     def set_counts(self, counts, mask=None) -> None:
         """``dode_set_counts``: new counts (and mask) for the loaded days; speeds and state kept."""
