@@ -64,6 +64,14 @@ def run(out_path: str) -> None:
     torch.cuda.synchronize()
     res["static_loss"] = ld.cpu().numpy()
     c.close()
+    # days copied ahead while a solve runs, then loaded from the device copies
+    c = dode.Context.from_workload(w7)
+    c.set_days(ct7, sp7, mk7)
+    c.prefetch_days(ct7, sp7, mk7)
+    c.solve(3, 5.0)
+    c.set_days(ct7, sp7, mk7)
+    res["prefetch_q"], res["prefetch_loss"] = c.solve(6, 5.0)
+    c.close()
     # the plain form
     c = dode.Context.from_workload(w7, form=dode.FORM_PLAIN)
     c.set_days(ct7, sp7, mk7)

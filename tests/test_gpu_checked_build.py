@@ -5,7 +5,7 @@ access, so a bad index never reaches memory (the stand-in for a memory
 sanitizer, which this GPU pool does not offer).  The cases of
 tests/checked_cases.py (every fused launch shape, both precisions, row chunks,
 epoch slices, coupled days, traffic patterns, R^2, DAR distance, the
-static-scratch loss, the plain form and the three dense methods, on ragged
+static-scratch loss, prefetched days, the plain form and the three dense methods, on ragged
 sizes) run through the checked build and through the normal build, each in a
 child process: the checked run must trip no check, and every result must be
 bitwise the normal build's, except where the normal build itself varies from
