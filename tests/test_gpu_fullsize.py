@@ -1,7 +1,8 @@
 """The full 3-year corridor workload (1096 days x 288 intervals, 150 OD pairs,
 300 routes, 400 detectors, 10 % missing) in the launch configuration the
-benchmark times, checked on sampled days against the FP64 oracle, which
-replays each sampled day on its own."""
+benchmark times (one persistent launch over all days; at 64 epochs the same 16
+epoch slices per day as the benchmark's 500), checked on sampled days against
+the FP64 oracle, which replays each sampled day on its own."""
 import numpy as np
 import pytest
 
@@ -44,6 +45,22 @@ def test_full_workload_sampled_days(full, precision):
     else:
         print(f"BF16 full-size sampled days: loss rel err {err_l.max():.2e}, q rel err {err_q.max():.2e}")
         assert err_l.max() < 2e-3 and err_q.max() < 2e-2
+
+
+def test_full_workload_sliced_epochs_sampled_days(full):
+    w, net, sp, counts, mask = full
+    epochs = 64
+    ctx = dode.Context.from_workload(w)
+    ctx.set_days(counts, sp, mask)
+    q, loss = ctx.solve(epochs, 5.0, batch=64)
+    assert ctx.last_slices() == 16 and ctx.last_launches() == 1
+    s = SAMPLE
+    qo, _, lo = net.solve_days(sp[s], counts[s], mask[s], iters=epochs, eta=5.0, day_ids=s, n_threads=len(s))
+    err_l = np.abs(loss[s] - lo) / lo
+    err_q = rel_norm(q[s], qo, axis=(1, 2))
+    print(f"64 epochs, 16 slices: loss rel err {err_l.max():.2e}, q rel err {err_q.max():.2e}")
+    assert err_l.max() < 1e-5, err_l
+    assert err_q.max() < 1e-4, err_q
 
 
 def test_full_workload_forward_sampled_days(full):
